@@ -1,0 +1,207 @@
+"""Seeded synthetic inputs shared by the CUDA library, the oracle, the tests and the bench.
+
+This module only *generates inputs*: hole lists, voxel images, source and observer
+positions, and the named workload configurations.  It contains none of the solver's
+arithmetic (no basis functions, quadrature, matrices or time stepping), so that the
+oracle and the CUDA path stay independent and both can be fed the same arrays.
+
+Randomness comes from SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom
+number generators", OOPSLA 2014): state += 0x9E3779B97F4A7C15, then the two
+xor-shift-multiply mixing rounds; doubles take the top 53 bits.
+
+Workloads (all on the unit square / cube, Neumann boundaries):
+
+* ``plate_one_hole`` - 2D scalar wave, one circular hole r=0.2 at the centre,
+  16x16 elements, p=2, alpha=1e-5, quadtree depth 3, Ricker point source f0=5.
+* ``plate_holes_elastic`` - 2D plane-strain elastodynamics (E=1, nu=0.3, rho=1),
+  12 seeded holes r in [0.02, 0.08], 256x256 elements, p=4, eigenvalue
+  stabilisation (f_lambda=1e-2, eps=1e-4, alpha=1e-12), Ricker edge traction, 10k steps.
+* ``plate_holes_imex`` - 2D scalar wave on the same holes, 512x512, p=3, IMEX
+  (alpha=1e-12) against explicit with mass scaling.
+* ``porous_voxel`` - 3D scalar wave, 128^3 voxel image of random spherical voids
+  at >=30 % porosity, 64^3 elements, p=3, alpha=1e-5, eigenvalue stabilisation.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 generator (Steele et al. 2014)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
+
+
+def random_holes(count: int, r_min: float, r_max: float, seed: int,
+                 edge_margin: float = 0.02, gap: float = 0.01,
+                 max_tries: int = 100000) -> np.ndarray:
+    """Non-overlapping circles in the unit square by rejection sampling.
+
+    Each circle keeps ``r + edge_margin`` from the square's edges and a gap of at
+    least ``gap`` to every other circle.  Returns ``(count, 3)`` rows ``(cx, cy, r)``.
+    """
+    rng = SplitMix64(seed)
+    out = []
+    tries = 0
+    while len(out) < count:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("random_holes: could not place all holes")
+        r = rng.uniform(r_min, r_max)
+        m = r + edge_margin
+        cx = rng.uniform(m, 1.0 - m)
+        cy = rng.uniform(m, 1.0 - m)
+        ok = True
+        for (ox, oy, orr) in out:
+            if math.hypot(cx - ox, cy - oy) < r + orr + gap:
+                ok = False
+                break
+        if ok:
+            out.append((cx, cy, r))
+    return np.array(out, dtype=np.float64)
+
+
+def random_void_image(vn: int, r_min: float, r_max: float, porosity: float,
+                      seed: int, max_spheres: int = 100000) -> np.ndarray:
+    """Voxel image ``(vn, vn, vn)`` uint8, index order [z, y, x], 1 = void.
+
+    Spheres with radius uniform in ``[r_min, r_max]`` voxels and centres uniform in
+    the voxel box are carved (voxel centre strictly inside a sphere -> void) until
+    the void fraction reaches ``porosity``.
+    """
+    rng = SplitMix64(seed)
+    img = np.zeros((vn, vn, vn), dtype=np.uint8)
+    c = np.arange(vn, dtype=np.float64) + 0.5
+    target = porosity * vn ** 3
+    nvoid = 0
+    for _ in range(max_spheres):
+        if nvoid >= target:
+            break
+        r = rng.uniform(r_min, r_max)
+        cx = rng.uniform(0.0, vn)
+        cy = rng.uniform(0.0, vn)
+        cz = rng.uniform(0.0, vn)
+        lo = [max(0, int(math.floor(q - r))) for q in (cz, cy, cx)]
+        hi = [min(vn, int(math.ceil(q + r)) + 1) for q in (cz, cy, cx)]
+        zz = c[lo[0]:hi[0]][:, None, None]
+        yy = c[lo[1]:hi[1]][None, :, None]
+        xx = c[lo[2]:hi[2]][None, None, :]
+        inside = (xx - cx) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2 < r * r
+        sub = img[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+        nvoid += int(np.count_nonzero(inside & (sub == 0)))
+        sub[inside] = 1
+    return img
+
+
+def nearest_solid_point(img: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Centre of the solid voxel nearest to ``x`` (unit-cube coordinates)."""
+    vn = img.shape[0]
+    solid = np.argwhere(img == 0)  # rows (z, y, x)
+    centres = (solid[:, ::-1].astype(np.float64) + 0.5) / vn
+    d = np.sum((centres - x[None, :]) ** 2, axis=1)
+    return centres[int(np.argmin(d))]
+
+
+@dataclass
+class Workload:
+    """A named synthetic problem: grid, discretisation, geometry, source, steps."""
+    name: str
+    dim: int
+    n: tuple
+    p: int
+    physics: str                      # "scalar" or "elastic"
+    rho: float = 1.0
+    c: float = 1.0
+    E: float = 1.0
+    nu: float = 0.3
+    alpha: float = 1e-5
+    quad_depth: int = 3
+    holes: Optional[np.ndarray] = None   # (k, d+1) rows (centre..., r)
+    voxels: Optional[np.ndarray] = None  # uint8 [z, y, x], 1 = void
+    stab: str = "none"                # "none" | "evs" | "mass_scaling"
+    eps: float = 0.0
+    f_lambda: float = 1e-2
+    scheme: str = "cdm"               # "cdm" | "imex"
+    source: dict = field(default_factory=dict)
+    f0: float = 5.0
+    steps: int = 200
+    dt_factor: float = 0.9
+    observers: Optional[np.ndarray] = None
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def default_observers(dim: int) -> np.ndarray:
+    if dim == 2:
+        return np.array([[0.25, 0.25], [0.75, 0.25], [0.25, 0.75], [0.75, 0.75],
+                         [0.5, 0.9], [0.9, 0.5]], dtype=np.float64)
+    return np.array([[0.25, 0.25, 0.25], [0.75, 0.75, 0.75], [0.5, 0.5, 0.9],
+                     [0.9, 0.5, 0.5]], dtype=np.float64)
+
+
+def plate_one_hole() -> Workload:
+    return Workload(name="plate_one_hole_16x16_p2", dim=2, n=(16, 16), p=2,
+                    physics="scalar", alpha=1e-5, quad_depth=3,
+                    holes=np.array([[0.5, 0.5, 0.2]]), stab="none",
+                    source={"kind": "point", "x": [0.15, 0.5]}, f0=5.0, steps=200,
+                    observers=default_observers(2))
+
+
+def plate_holes_elastic(n: int = 256, p: int = 4, count: int = 12, seed: int = 0,
+                        steps: int = 10000) -> Workload:
+    holes = random_holes(count, 0.02, 0.08, seed)
+    return Workload(name=f"plate_holes_elastic_{n}x{n}_p{p}", dim=2, n=(n, n), p=p,
+                    physics="elastic", E=1.0, nu=0.3, rho=1.0, alpha=1e-12,
+                    quad_depth=3, holes=holes, stab="evs", eps=1e-4, f_lambda=1e-2,
+                    source={"kind": "edge_traction", "y0": 0.4, "y1": 0.6,
+                            "t": [1.0, 0.0]},
+                    f0=10.0, steps=steps, observers=default_observers(2))
+
+
+def plate_holes_imex(n: int = 512, p: int = 3, count: int = 12, seed: int = 0,
+                     steps: int = 1000, scheme: str = "imex") -> Workload:
+    holes = random_holes(count, 0.02, 0.08, seed)
+    return Workload(name=f"plate_holes_{scheme}_{n}x{n}_p{p}", dim=2, n=(n, n), p=p,
+                    physics="scalar", alpha=1e-12, quad_depth=3, holes=holes,
+                    stab="none" if scheme == "imex" else "mass_scaling",
+                    scheme=scheme, source={"kind": "point", "x": [0.1, 0.5]},
+                    f0=10.0, steps=steps, observers=default_observers(2))
+
+
+def porous_voxel(n: int = 64, vn: int = 128, p: int = 3, seed: int = 0,
+                 steps: int = 2000, porosity: float = 0.30) -> Workload:
+    img = random_void_image(vn, 4.0 * vn / 128.0, 12.0 * vn / 128.0, porosity, seed)
+    xs = nearest_solid_point(img, np.array([0.1, 0.5, 0.5]))
+    return Workload(name=f"porous_voxel_{n}^3_p{p}", dim=3, n=(n, n, n), p=p,
+                    physics="scalar", alpha=1e-5, quad_depth=1, voxels=img,
+                    stab="evs", eps=1e-4, f_lambda=1e-2,
+                    source={"kind": "point", "x": list(xs)}, f0=10.0, steps=steps,
+                    observers=default_observers(3))
+
+
+WORKLOADS = {
+    "plate_one_hole": plate_one_hole,
+    "plate_holes_elastic": plate_holes_elastic,
+    "plate_holes_imex": plate_holes_imex,
+    "porous_voxel": porous_voxel,
+}
