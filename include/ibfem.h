@@ -1,0 +1,220 @@
+/*
+ * ibfem.h -- C ABI of the GB300 immersed-boundary explicit wave solver.
+ *
+ * The library advances the semi-discrete wave equation M Psi'' + K Psi = F (Sec. 2.2,
+ * Eq. semi of Buerchner et al., arXiv 2501.19013) on a uniform Cartesian grid of
+ * tensor-product GLL spectral elements of order p, where cells cut by the immersed
+ * boundary carry the finite cell indicator alpha^FCM (Eq. weak_form_extended).  One
+ * time step of the explicit scheme is the central-difference update (Eq. cdm)
+ *
+ *     u^{k+1} = 2 u^k - u^{k-1} + dt^2 M_L^{-1} (F^k - K u^k),
+ *
+ * with K applied element by element on the GPU (no global matrix) and M_L the lumped
+ * mass.  The semi-explicit variant is the Newmark IMEX scheme of Algorithm 2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status: IBFEM_OK (0) or a negative IBFEM_ERR_* code.
+ *    On error a human-readable message is available from ibfem_last_error() (per
+ *    thread) and the handle stays valid unless stated otherwise.
+ *  - Host arrays passed in are copied before the call returns; the caller keeps
+ *    ownership.  Output arrays are caller-allocated host memory of the stated size.
+ *  - Vectors in the ABI ("kept-DOF order") are indexed by the kept DOFs: the global node
+ *    lattice has (n_k p + 1) nodes per axis, numbered lexicographically with x fastest;
+ *    nodes that belong to at least one kept (not entirely fictitious) cell are numbered
+ *    in lattice order; the ncomp components of a node are consecutive.
+ *  - Device memory belongs to the handle.  It is obtained through options->dev_alloc
+ *    (e.g. the PyTorch caching allocator) when given, else cudaMalloc.
+ *  - ibfem_step only enqueues work on the handle's stream; ibfem_sample, ibfem_get_state,
+ *    ibfem_crit_dt, ibfem_sync and the other "read" calls synchronise that stream.
+ *  - Handles are not thread-safe; distinct handles may be used from distinct threads.
+ */
+#ifndef IBFEM_H
+#define IBFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define IBFEM_OK 0
+#define IBFEM_ERR_ARG (-1)       /* invalid argument or unsupported combination        */
+#define IBFEM_ERR_OOM (-2)       /* device or host allocation failed                   */
+#define IBFEM_ERR_CUDA (-3)      /* a CUDA runtime call failed                         */
+#define IBFEM_ERR_DIVERGED (-4)  /* a non-finite value appeared in the state           */
+#define IBFEM_ERR_TIMEOUT (-5)   /* a bounded device wait gave up                      */
+#define IBFEM_ERR_GEOMETRY (-6)  /* geometry leaves no kept cell / point not in domain */
+#define IBFEM_ERR_EIG (-7)       /* a host eigen/Cholesky factorisation failed         */
+#define IBFEM_ERR_STATE (-8)     /* call order (e.g. step before set_dt)               */
+
+/* ---- enumerations ---------------------------------------------------------------- */
+enum { IBFEM_GEOM_NONE = 0,     /* no immersed boundary: every cell is uncut            */
+       IBFEM_GEOM_HOLES = 1,    /* circles (2D) / spheres (3D) of fictitious material   */
+       IBFEM_GEOM_VOXELS = 2,   /* voxel image, 1 = void (fictitious), 0 = solid        */
+       IBFEM_GEOM_ROTATED_BOX = 3 /* physical domain = rotated cube (Sec. 3.1)          */ };
+enum { IBFEM_STAB_NONE = 0, IBFEM_STAB_EVS = 1, IBFEM_STAB_MASS_SCALING = 2 };
+enum { IBFEM_SCALAR = 0, IBFEM_ELASTIC_PLANE_STRAIN = 1 };
+enum { IBFEM_CDM = 0, IBFEM_IMEX = 1 };
+/* Precision of the element contractions.  The integrator state (u^k, u^{k-1}), the
+ * central-difference update, the IMEX solves and the power iteration are FP64 always. */
+enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores                  */
+       IBFEM_TF32X3_TC = 1,     /* tcgen05 kind::tf32, 3-pass split (about FP32)        */
+       IBFEM_TF32_TC = 2,       /* tcgen05 kind::tf32, one pass                         */
+       IBFEM_BF16_TC = 3        /* tcgen05 kind::f16 with BF16 operands, FP32 accum     */ };
+enum { IBFEM_SRC_NONE = 0,
+       IBFEM_SRC_POINT = 1,          /* params: x, y[, z] [, dir_x, dir_y] (elastic)   */
+       IBFEM_SRC_EDGE_TRACTION = 2   /* params: y0, y1, t_x[, t_y]; edge x = lo_x (2D) */ };
+
+/* ---- structures ------------------------------------------------------------------ */
+typedef struct ibfem_s ibfem_t;
+
+typedef struct {
+    int dim;          /* 2 or 3                                                        */
+    int n[3];         /* cells per axis (n[2] ignored in 2D)                           */
+    double lo[3];     /* extended-domain box                                           */
+    double hi[3];
+} ibfem_grid;
+
+typedef struct {
+    int kind;                 /* IBFEM_GEOM_*                                          */
+    int count;                /* HOLES: number of circles/spheres                      */
+    const double* shapes;     /* HOLES: count x (cx, cy[, cz], r);
+                                 ROTATED_BOX: (edge, cx, cy, cz, T00..T22 row-major),
+                                 T maps the cube frame to global axes (x = c + T x')   */
+    const uint8_t* voxels;    /* VOXELS: vn[0]*vn[1]*vn[2] bytes, x fastest, 1 = void  */
+    int vn[3];                /* VOXELS: voxels per axis spanning [lo, hi]             */
+    int quad_depth;           /* space-tree depth for cut cells (>= 0)                 */
+} ibfem_geometry;
+
+typedef struct {
+    int kind;                 /* IBFEM_STAB_*                                          */
+    double eps;               /* EVS: epsilon of Eq. epsilon_stabilization             */
+    double f_lambda;          /* EVS: small-eigenvalue threshold fraction              */
+} ibfem_stab;
+
+typedef struct {
+    int physics;              /* IBFEM_SCALAR or IBFEM_ELASTIC_PLANE_STRAIN (2D only)  */
+    double rho, c;            /* density, wave speed (scalar)                          */
+    double E, nu;             /* Young's modulus, Poisson ratio (elastic)              */
+    int scheme;               /* IBFEM_CDM or IBFEM_IMEX                               */
+    int precision;            /* IBFEM_FP64 / _TF32X3_TC / _TF32_TC / _BF16_TC         */
+    void* stream;             /* cudaStream_t to run on, NULL = the legacy stream      */
+    void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator         */
+    void (*dev_free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+    int device;               /* CUDA device ordinal, made current inside every call   */
+    int host_only;            /* 1: build the host discretisation only (no device use);
+                                 only ibfem_info/get_lumped_mass/get_cut_cells/
+                                 get_element are then valid -- for checks without a GPU */
+} ibfem_options;
+
+typedef struct {
+    int64_t n_dof;            /* kept DOFs                                             */
+    int64_t n_lattice_dof;    /* DOFs of the full node lattice (device layout)         */
+    int64_t n_elem, n_uncut, n_cut, n_outside;
+    int64_t n_c;              /* IMEX: DOFs treated implicitly (0 for CDM)             */
+    int64_t nnz_L;            /* IMEX: nonzeros of the Cholesky factor                 */
+    int32_t n_levels;         /* IMEX: level count of the forward solve                */
+    int32_t n_loc;            /* DOFs per element                                      */
+    int32_t ncomp;
+    int32_t precision;
+    int64_t step;             /* steps taken since set_initial / set_state             */
+    double t, dt;
+    double lambda_ref;        /* lambda_max(K_ref, M_ref) of one uncut cell            */
+    size_t device_bytes;      /* device memory held by the handle                      */
+} ibfem_info_t;
+
+/* ---- lifetime -------------------------------------------------------------------- */
+
+/* Build the discretisation (Sec. 2.2-2.6) on the host and upload it.
+ *  grid, p (1..6), geometry (NULL = none), alpha (indicator value in the fictitious
+ *  domain, Eq. weak_form_extended), stab (NULL = none), opt (NULL = scalar, rho = c = 1,
+ *  CDM, FP64, default stream and allocator).  *out receives the new handle.
+ *  Errors: ARG (bad sizes/combination), GEOMETRY (no kept cell), EIG (a cut-cell
+ *  eigenproblem or the IMEX factorisation failed), OOM, CUDA.                          */
+int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry,
+                 double alpha, const ibfem_stab* stab, const ibfem_options* opt,
+                 ibfem_t** out);
+/* Free every resource of the handle (NULL is accepted). */
+int ibfem_destroy(ibfem_t* h);
+/* Message of the last failed call on this thread ("" if none).  Valid until the next
+ * failing call on the same thread. */
+const char* ibfem_last_error(void);
+int ibfem_info(const ibfem_t* h, ibfem_info_t* out);
+
+/* ---- problem data ---------------------------------------------------------------- */
+
+/* Load F^k = F_s * f_t(t_k) with the Ricker wavelet of Eq. source_time (centre
+ * frequency f_e).  kind/params as in IBFEM_SRC_*.  A point source contributes
+ * alpha^FCM(x_s) rho N_i(x_s) (times the direction for elasticity); an edge traction
+ * contributes the boundary integral of alpha^FCM N_i t.  Errors: ARG, GEOMETRY.        */
+int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, double f_e);
+
+/* Observer points (Sec. 3.2): npts x dim coordinates.  Each step records
+ * Psi(x_i, t_k) = sum_j N_j(x_i) u_j^k (all components) into a device ring of
+ * `capacity` rows; ibfem_sample returns them.  Resets the ring.  Errors: ARG, GEOMETRY. */
+int ibfem_set_observers(ibfem_t* h, int npts, const double* xyz, int64_t capacity);
+
+/* Initial state Psi_0, Psi'_0 (host, kept-DOF order, n_dof each; NULL = zero).  The
+ * start-up value u^{-1} = u^0 - dt v^0 + dt^2/2 M_L^{-1}(F^0 - K u^0) is formed on the
+ * device (IMEX: its d-part, plus Psi''_0 on the c-part from M^cc).  Requires set_dt.   */
+int ibfem_set_initial(ibfem_t* h, const double* u0, const double* v0);
+
+/* Critical step dt_crit = 2 / sqrt(lambda_max(K, M_L)) (Sec. 2.3) by power iteration on
+ * M_L^{-1/2} K M_L^{-1/2}: start v_i = 1 + 0.5 sin(i) over kept DOFs, stop when
+ * |lambda_k - lambda_{k-1}| <= rtol lambda_k or after max_iter products.  For IMEX the
+ * iteration runs on the explicit (d) block.  Any of the outputs may be NULL.           */
+int ibfem_crit_dt(ibfem_t* h, int max_iter, double rtol, double* dt_crit,
+                  double* lambda_max, int* iterations);
+
+/* Set the step size (> 0).  Rescales dt^2 M_L^{-1} on the device and, for IMEX,
+ * refactors S = M^cc + dt^2/4 K^cc on the host.  Errors: ARG, EIG.                     */
+int ibfem_set_dt(ibfem_t* h, double dt);
+
+/* ---- time stepping --------------------------------------------------------------- */
+
+/* Enqueue n steps (n >= 0) on the handle's stream, replaying a captured CUDA graph of
+ * the per-step kernels.  Asynchronous.  Errors: STATE (no dt / initial), CUDA.         */
+int ibfem_step(ibfem_t* h, int64_t n);
+
+/* Same as ibfem_step, but every kernel is launched directly with a pair of CUDA events
+ * around it on the handle's stream (no graph).  ms[slot] accumulates the device time of
+ * kernel slot `slot` (at most max_slots slots, names from ibfem_kernel_name); *n_slots
+ * receives the slot count.  Synchronises.  Meant for benchmarks and profiles.           */
+int ibfem_step_timed(ibfem_t* h, int64_t n, double* ms, int max_slots, int* n_slots);
+/* Name of kernel slot `slot` of ibfem_step_timed ("" if out of range). */
+const char* ibfem_kernel_name(const ibfem_t* h, int slot);
+
+/* Synchronise the stream and report a non-finite state as IBFEM_ERR_DIVERGED. */
+int ibfem_sync(ibfem_t* h);
+
+/* Observer series recorded since set_observers/set_initial, oldest first: up to
+ * max_rows rows of npts*ncomp doubles (row r = time t_{k0+r}).  The last row is the
+ * current state Psi(t_k).  *rows receives the count.  Synchronises.                    */
+int ibfem_sample(ibfem_t* h, int64_t max_rows, double* out, int64_t* rows);
+
+/* State (host, kept-DOF order, n_dof each; either pointer may be NULL). Synchronises.
+ * CDM: u = u^k, u_prev = u^{k-1}.  IMEX: u_prev holds u^{k-1} on d and Psi'^k on c.     */
+int ibfem_get_state(ibfem_t* h, double* u, double* u_prev);
+/* Restore a state previously read by ibfem_get_state together with its step index. */
+int ibfem_set_state(ibfem_t* h, const double* u, const double* u_prev, int64_t step);
+
+/* ---- inspection (used by the parity tests) ---------------------------------------- */
+
+/* y = K x with x, y in kept-DOF order (host).  Synchronises. */
+int ibfem_apply_operator(ibfem_t* h, const double* x, double* y);
+/* Assembled lumped mass diagonal M_L (kept-DOF order, n_dof doubles). */
+int ibfem_get_lumped_mass(ibfem_t* h, double* ml);
+/* Flat indices (x fastest) of the cut cells, n_cut int64 values in ascending order. */
+int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells);
+/* Element stiffness (n_loc x n_loc, row-major) used for cell `cell` (shared reference
+ * matrix for uncut cells); optional lumped diagonal (n_loc). Errors: ARG (outside).   */
+int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBFEM_H */

@@ -43,7 +43,7 @@ def ricker(t, f_e):
 class Discretization:
     def __init__(self, dim, n, p, physics="scalar", geometry=None, alpha=1e-5,
                  quad_depth=3, stab="none", eps=0.0, f_lambda=1e-2, rho=1.0, c=1.0,
-                 E=1.0, nu=0.3, lo=None, hi=None):
+                 E=1.0, nu=0.3, lo=None, hi=None, assemble=True):
         self.dim = dim
         self.n = np.array(n[:dim], dtype=int)
         self.p = p
@@ -66,8 +66,12 @@ class Discretization:
         self.lat = self.n * p + 1                     # lattice nodes per axis
         self._classify()
         self._number()
-        self._element_matrices()
-        self._assemble()
+        self._reference_matrices()
+        self.K_cut, self.M_cut_cons, self.M_cut_stab, self.ml_cut, self.scale_cut = {}, {}, {}, {}, {}
+        if assemble:
+            for e in self.cut:
+                self._cut_matrices(e)
+            self._assemble()
 
     # ---------------------------------------------------------------- geometry
     def elem_coords(self, e):
@@ -131,39 +135,92 @@ class Discretization:
             return el.elastic_matrices(self.p, lo, hi, X, W, A, self.rho, self.E, self.nu)
         return el.scalar_matrices(self.p, lo, hi, X, W, A, self.rho, self.c)
 
-    def _element_matrices(self):
+    def _reference_matrices(self):
         lo0 = self.lo
         hi0 = self.lo + self.h
         X, W, A = full_cell_quadrature(lo0, hi0, self.p)
         self.K_ref, self.M_full = self._matrices(lo0, hi0, X, W, A)
         self.m_gll = el.gll_mass_diagonal(self.p, self.h, self.rho, self.ncomp)
         self.lam_ref = element_lambda_max(self.K_ref, self.m_gll)
-        self.K_cut = {}
-        self.M_cut_cons = {}   # alpha-FCM consistent (unstabilised) mass
-        self.M_cut_stab = {}   # after eigenvalue stabilisation (= cons without EVS)
-        self.ml_cut = {}       # HRZ-lumped (and possibly mass-scaled) diagonal
-        self.scale_cut = {}
-        for e in self.cut:
-            lo, hi = self.elem_box(e)
-            X, W, A = cut_cell_quadrature(self.geom, lo, hi, self.p, self.quad_depth, self.alpha)
-            K, M = self._matrices(lo, hi, X, W, A)
-            self.K_cut[e] = K
-            self.M_cut_cons[e] = M
-            Ms = evs(M, self.M_full, self.eps, self.f_lambda) if self.stab == "evs" else M
-            self.M_cut_stab[e] = Ms
-            ml = hrz(Ms)
-            s = 1.0
-            if self.stab == "mass_scaling":
-                s = mass_scaling_factor(K, ml, self.lam_ref)
-                ml = s * ml
-            self.scale_cut[e] = s
-            self.ml_cut[e] = ml
+
+    def _cut_matrices(self, e):
+        """K^e, consistent M^e (alpha), stabilised M^e and the HRZ-lumped diagonal of a
+        cut cell (stored in K_cut, M_cut_cons, M_cut_stab, ml_cut, scale_cut)."""
+        lo, hi = self.elem_box(e)
+        X, W, A = cut_cell_quadrature(self.geom, lo, hi, self.p, self.quad_depth, self.alpha)
+        K, M = self._matrices(lo, hi, X, W, A)
+        self.K_cut[e] = K
+        self.M_cut_cons[e] = M
+        Ms = evs(M, self.M_full, self.eps, self.f_lambda) if self.stab == "evs" else M
+        self.M_cut_stab[e] = Ms
+        ml = hrz(Ms)
+        s = 1.0
+        if self.stab == "mass_scaling":
+            s = mass_scaling_factor(K, ml, self.lam_ref)
+            ml = s * ml
+        self.scale_cut[e] = s
+        self.ml_cut[e] = ml
 
     def elem_K(self, e):
-        return self.K_cut[e] if self.cls[e] == CUT else self.K_ref
+        if self.cls[e] == CUT:
+            if e not in self.K_cut:
+                self._cut_matrices(e)
+            return self.K_cut[e]
+        return self.K_ref
 
     def elem_ml(self, e):
-        return self.ml_cut[e] if self.cls[e] == CUT else self.m_gll
+        if self.cls[e] == CUT:
+            if e not in self.ml_cut:
+                self._cut_matrices(e)
+            return self.ml_cut[e]
+        return self.m_gll
+
+    def cells_of_dof(self, dof):
+        """Kept cells whose nodes include the DOF's node (ascending), with local index."""
+        node = dof // self.ncomp
+        comp = dof % self.ncomp
+        lat = self.lattice_of_node[node]
+        g = []
+        for k in range(self.dim):
+            g.append(lat % self.lat[k])
+            lat //= self.lat[k]
+        out = []
+        for offs in np.ndindex(*([2] * self.dim)):
+            ij = [g[k] // self.p - offs[k] for k in range(self.dim)]
+            if any(ij[k] < 0 or ij[k] >= self.n[k] for k in range(self.dim)):
+                continue
+            a = [g[k] - ij[k] * self.p for k in range(self.dim)]
+            if any(a[k] < 0 or a[k] > self.p for k in range(self.dim)):
+                continue
+            e = 0
+            stride = 1
+            for k in range(self.dim):
+                e += ij[k] * stride
+                stride *= self.n[k]
+            if self.cls[e] == OUTSIDE:
+                continue
+            loc = 0
+            stride = 1
+            for k in range(self.dim):
+                loc += a[k] * stride
+                stride *= self.p + 1
+            out.append((e, loc * self.ncomp + comp))
+        return sorted(set(out))
+
+    def local_cdm_update(self, dofs, u, u_prev, dt, fk=None):
+        """Eq. cdm evaluated at selected DOFs only, from element contributions of the
+        cells that contain them (no assembly): u_i^{k+1} for i in dofs."""
+        out = np.zeros(len(dofs))
+        for n_, i in enumerate(dofs):
+            ku = 0.0
+            m = 0.0
+            for e, loc in self.cells_of_dof(i):
+                D = self.elem_dofs[e]
+                ku += self.elem_K(e)[loc] @ u[D]
+                m += self.elem_ml(e)[loc]
+            f = 0.0 if fk is None else fk[n_]
+            out[n_] = 2.0 * u[i] - u_prev[i] + dt * dt / m * (f - ku)
+        return out
 
     def _assemble(self):
         rows, cols, vals = [], [], []

@@ -1,0 +1,789 @@
+// Host construction of the spectral cell discretisation (library side).
+//
+// Sec. 2.2 (spatial discretisation, finite cell indicator, space-tree quadrature of cut
+// cells), Sec. 2.4 (nodal lumping of uncut cells, HRZ lumping of cut cells), Sec. 2.5
+// (eigenvalue stabilisation, Eq. epsilon_stabilization) of Buerchner et al.,
+// arXiv 2501.19013.  Plane-strain elasticity and mass scaling are not defined in the
+// paper; their textbook forms are used (isotropic Lame operator; cut-cell mass scaled by
+// max(1, lambda_e / lambda_ref)).
+//
+// 1D rules come from the Golub-Welsch eigenvalue method: Gauss-Legendre nodes are the
+// eigenvalues of the Legendre Jacobi matrix, the interior Gauss-Lobatto-Legendre nodes
+// those of the Jacobi matrix of P^{(1,1)} (roots of P_p').
+#include "host_setup.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <stdexcept>
+#include <thread>
+
+namespace ibfem {
+
+namespace {
+
+// ------------------------------------------------------------------ 1D rules
+// Symmetric tridiagonal Golub-Welsch: diag zero, off-diagonal b[k]; returns nodes and
+// the squared first eigenvector components (times mu0 gives the weights).
+void golub_welsch(int m, const std::vector<double>& off, std::vector<double>& x,
+                  std::vector<double>& v0sq) {
+  std::vector<double> A(m * m, 0.0), V(m * m), ev(m);
+  for (int k = 0; k + 1 < m; ++k) {
+    A[k * m + k + 1] = off[k];
+    A[(k + 1) * m + k] = off[k];
+  }
+  if (!sym_eig(m, A.data(), ev.data(), V.data()))
+    throw std::runtime_error("Golub-Welsch eigenproblem did not converge");
+  x = ev;
+  v0sq.resize(m);
+  for (int j = 0; j < m; ++j) v0sq[j] = V[0 * m + j] * V[0 * m + j];
+}
+
+void gauss_rule(int m, std::vector<double>& x, std::vector<double>& w) {
+  std::vector<double> off(std::max(m - 1, 0));
+  for (int k = 1; k < m; ++k) off[k - 1] = k / std::sqrt(4.0 * k * k - 1.0);
+  std::vector<double> v0;
+  golub_welsch(m, off, x, v0);
+  w.resize(m);
+  for (int j = 0; j < m; ++j) w[j] = 2.0 * v0[j];
+}
+
+double legendre(int n, double x) {
+  double a = 1.0, b = x;
+  if (n == 0) return 1.0;
+  for (int k = 1; k < n; ++k) {
+    double c = ((2 * k + 1) * x * b - k * a) / (k + 1);
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+void gll_rule(int p, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(p + 1, 0.0);
+  x[0] = -1.0;
+  x[p] = 1.0;
+  if (p >= 2) {
+    int m = p - 1;  // interior nodes: zeros of the Jacobi polynomial P^{(1,1)}_{p-1}
+    std::vector<double> off(std::max(m - 1, 0));
+    for (int k = 1; k < m; ++k) off[k - 1] = std::sqrt(k * (k + 2.0) / ((2.0 * k + 1.0) * (2.0 * k + 3.0)));
+    std::vector<double> xi, v0;
+    golub_welsch(m, off, xi, v0);
+    for (int j = 0; j < m; ++j) x[j + 1] = xi[j];
+  }
+  w.resize(p + 1);
+  for (int j = 0; j <= p; ++j) {
+    double P = legendre(p, x[j]);
+    w[j] = 2.0 / (p * (p + 1.0) * P * P);
+  }
+}
+
+// 1D Lagrange values and derivatives at t for the nodes xs (product form).
+void lagrange1d(const std::vector<double>& xs, double t, double* L, double* dL) {
+  int m = (int)xs.size();
+  for (int a = 0; a < m; ++a) {
+    double val = 1.0, der = 0.0;
+    for (int b = 0; b < m; ++b) {
+      if (b == a) continue;
+      double inv = 1.0 / (xs[a] - xs[b]);
+      // d/dt of the running product (t - x_b) / (x_a - x_b)
+      der = der * (t - xs[b]) * inv + val * inv;
+      val *= (t - xs[b]) * inv;
+    }
+    L[a] = val;
+    if (dL) dL[a] = der;
+  }
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geo {
+  const SetupInput* in;
+  int d;
+  // rotated box
+  double half = 0, c[3] = {0, 0, 0}, T[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+
+  explicit Geo(const SetupInput& inp) : in(&inp), d(inp.dim) {
+    if (inp.geom.kind == 3) {
+      const auto& s = inp.geom.shapes;
+      half = 0.5 * s[0];
+      for (int k = 0; k < 3; ++k) c[k] = s[1 + k];
+      for (int k = 0; k < 9; ++k) T[k] = s[4 + k];
+    }
+  }
+
+  bool physical_point(const double* x) const {
+    const auto& g = in->geom;
+    if (g.kind == 1) {
+      int stride = d + 1;
+      int cnt = (int)(g.shapes.size() / stride);
+      for (int i = 0; i < cnt; ++i) {
+        const double* s = &g.shapes[i * stride];
+        double r2 = 0;
+        for (int k = 0; k < d; ++k) r2 += (x[k] - s[k]) * (x[k] - s[k]);
+        if (r2 < s[d] * s[d]) return false;
+      }
+      return true;
+    }
+    if (g.kind == 2) {
+      int64_t idx = 0, stride = 1;
+      for (int k = 0; k < d; ++k) {
+        double rel = (x[k] - in->lo[k]) / (in->hi[k] - in->lo[k]) * g.vn[k];
+        int64_t i = (int64_t)std::floor(rel);
+        i = std::min<int64_t>(std::max<int64_t>(i, 0), g.vn[k] - 1);
+        idx += i * stride;
+        stride *= g.vn[k];
+      }
+      return g.voxels[idx] == 0;
+    }
+    if (g.kind == 3) {
+      for (int a = 0; a < 3; ++a) {
+        double loc = 0;
+        for (int k = 0; k < 3; ++k) loc += (x[k] - c[k]) * T[k * 3 + a];
+        if (std::fabs(loc) > half) return false;
+      }
+      return true;
+    }
+    return true;
+  }
+
+  // Box classification.  Voxel boxes are given by integer coordinates in units of
+  // 1/(n_k 2^level) of the extended domain so that voxel ranges are exact.
+  CellClass classify(const double* blo, const double* bhi, const int64_t* ilo,
+                     int64_t denom_scale) const {
+    const auto& g = in->geom;
+    if (g.kind == 0) return kUncut;
+    if (g.kind == 1) {
+      int stride = d + 1;
+      int cnt = (int)(g.shapes.size() / stride);
+      bool cut = false;
+      for (int i = 0; i < cnt; ++i) {
+        const double* s = &g.shapes[i * stride];
+        double dmin2 = 0, dmax2 = 0;
+        for (int k = 0; k < d; ++k) {
+          double gap = std::max(std::max(blo[k] - s[k], 0.0), s[k] - bhi[k]);
+          dmin2 += gap * gap;
+          double far = std::max(std::fabs(s[k] - blo[k]), std::fabs(s[k] - bhi[k]));
+          dmax2 += far * far;
+        }
+        double r2 = s[d] * s[d];
+        if (dmax2 <= r2) return kOutside;
+        if (dmin2 < r2) cut = true;
+      }
+      return cut ? kCut : kUncut;
+    }
+    if (g.kind == 2) {
+      // voxel index range [v0, v1) per axis from exact integer arithmetic:
+      // box spans [ilo, ilo+1] in units of h/denom_scale of the cell grid.
+      int64_t v0[3] = {0, 0, 0}, v1[3] = {1, 1, 1};
+      for (int k = 0; k < d; ++k) {
+        int64_t den = (int64_t)in->n[k] * denom_scale;
+        int64_t a = ilo[k] * g.vn[k];
+        int64_t b = (ilo[k] + 1) * g.vn[k];
+        v0[k] = a / den;
+        v1[k] = (b + den - 1) / den;
+        v0[k] = std::min<int64_t>(std::max<int64_t>(v0[k], 0), g.vn[k] - 1);
+        v1[k] = std::min<int64_t>(std::max<int64_t>(v1[k], v0[k] + 1), g.vn[k]);
+      }
+      bool any_void = false, any_solid = false;
+      for (int64_t z = v0[2]; z < (d == 3 ? v1[2] : 1); ++z)
+        for (int64_t y = v0[1]; y < v1[1]; ++y)
+          for (int64_t x = v0[0]; x < v1[0]; ++x) {
+            int64_t idx = x + (int64_t)g.vn[0] * (y + (int64_t)g.vn[1] * z);
+            if (g.voxels[idx]) any_void = true; else any_solid = true;
+            if (any_void && any_solid) return kCut;
+          }
+      return any_solid ? kUncut : kOutside;
+    }
+    // rotated box: separating axes between the aligned box and the cube
+    double cb[3], hb[3];
+    for (int k = 0; k < 3; ++k) {
+      cb[k] = 0.5 * (blo[k] + bhi[k]);
+      hb[k] = 0.5 * (bhi[k] - blo[k]);
+    }
+    double axes[15][3];
+    int na = 0;
+    for (int k = 0; k < 3; ++k) {
+      for (int j = 0; j < 3; ++j) axes[na][j] = (j == k) ? 1.0 : 0.0;
+      ++na;
+    }
+    for (int k = 0; k < 3; ++k) {
+      for (int j = 0; j < 3; ++j) axes[na][j] = T[j * 3 + k];
+      ++na;
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) {
+        double e[3] = {0, 0, 0};
+        e[i] = 1.0;
+        double t[3] = {T[0 * 3 + k], T[1 * 3 + k], T[2 * 3 + k]};
+        double cr[3] = {e[1] * t[2] - e[2] * t[1], e[2] * t[0] - e[0] * t[2], e[0] * t[1] - e[1] * t[0]};
+        double nrm = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        if (nrm > 1e-12) {
+          for (int j = 0; j < 3; ++j) axes[na][j] = cr[j] / nrm;
+          ++na;
+        }
+      }
+    for (int a = 0; a < na; ++a) {
+      const double* L = axes[a];
+      double rb = 0, rc = 0, proj = 0;
+      for (int k = 0; k < 3; ++k) {
+        rb += hb[k] * std::fabs(L[k]);
+        proj += (c[k] - cb[k]) * L[k];
+      }
+      for (int j = 0; j < 3; ++j) {
+        double tl = T[0 * 3 + j] * L[0] + T[1 * 3 + j] * L[1] + T[2 * 3 + j] * L[2];
+        rc += half * std::fabs(tl);
+      }
+      if (std::fabs(proj) >= rb + rc) return kOutside;
+    }
+    for (int corner = 0; corner < 8; ++corner) {
+      double x[3];
+      for (int k = 0; k < 3; ++k) x[k] = (corner >> k) & 1 ? bhi[k] : blo[k];
+      if (!physical_point(x)) return kCut;
+    }
+    return kUncut;
+  }
+};
+
+// ------------------------------------------------------------------ element integration
+struct ElementIntegrator {
+  const Setup* s;
+  const SetupInput* in;
+  std::vector<double> gx, gw;  // GL rule with p + 1 points
+
+  ElementIntegrator(const Setup& st, const SetupInput& inp) : s(&st), in(&inp) {
+    gauss_rule(st.p + 1, gx, gw);
+  }
+
+  // Accumulate K and M (n_loc x n_loc, full) over a tensor GL rule on the sub-box
+  // [blo, bhi] of the cell [clo, clo + h]; alpha: constant (>= 0) or pointwise (< 0).
+  void accumulate(const Geo& geo, const double* clo, const double* blo, const double* bhi,
+                  double alpha_const, double* K, double* M) const {
+    const int d = s->dim, m = s->nn1, nq1 = (int)gx.size();
+    const int nnl = s->nn_loc, nc = s->ncomp, nl = s->n_loc;
+    int nq = 1;
+    for (int k = 0; k < d; ++k) nq *= nq1;
+    std::vector<double> Lv(d * m), Ld(d * m), N(nnl), G(d * nnl);
+    double lam = 0, mu = 0;
+    if (s->ncomp == 2) {
+      lam = in->E * in->nu / ((1 + in->nu) * (1 - 2 * in->nu));
+      mu = in->E / (2 * (1 + in->nu));
+    }
+    for (int q = 0; q < nq; ++q) {
+      double x[3] = {0, 0, 0}, w = 1.0;
+      int qq = q;
+      for (int k = 0; k < d; ++k) {
+        int i = qq % nq1;
+        qq /= nq1;
+        double half = 0.5 * (bhi[k] - blo[k]);
+        x[k] = blo[k] + (gx[i] + 1.0) * half;
+        w *= gw[i] * half;
+        double t = 2.0 * (x[k] - clo[k]) / s->h[k] - 1.0;
+        lagrange1d(s->gll_x, t, &Lv[k * m], &Ld[k * m]);
+        for (int a = 0; a < m; ++a) Ld[k * m + a] *= 2.0 / s->h[k];
+      }
+      double a = alpha_const >= 0 ? alpha_const : (geo.physical_point(x) ? 1.0 : in->alpha);
+      double wa = w * a;
+      if (wa == 0.0) continue;
+      for (int j = 0; j < nnl; ++j) {
+        int jj = j;
+        double nv = 1.0, g[3] = {1.0, 1.0, 1.0};
+        for (int k = 0; k < d; ++k) {
+          int ak = jj % m;
+          jj /= m;
+          nv *= Lv[k * m + ak];
+          for (int l = 0; l < d; ++l) g[l] *= (l == k ? Ld[k * m + ak] : Lv[k * m + ak]);
+        }
+        N[j] = nv;
+        for (int l = 0; l < d; ++l) G[l * nnl + j] = g[l];
+      }
+      if (nc == 1) {
+        double kc = in->rho * in->c * in->c * wa, mc = in->rho * wa;
+        for (int i = 0; i < nnl; ++i)
+          for (int j = i; j < nnl; ++j) {
+            double gg = 0;
+            for (int l = 0; l < d; ++l) gg += G[l * nnl + i] * G[l * nnl + j];
+            K[i * nl + j] += kc * gg;
+            M[i * nl + j] += mc * N[i] * N[j];
+          }
+      } else {
+        // plane strain: K_(ia)(jb) = lam d_a N_i d_b N_j + mu d_b N_i d_a N_j
+        //                            + mu delta_ab grad N_i . grad N_j
+        double mc = in->rho * wa;
+        for (int i = 0; i < nnl; ++i)
+          for (int j = 0; j < nnl; ++j) {
+            double gg = G[0 * nnl + i] * G[0 * nnl + j] + G[1 * nnl + i] * G[1 * nnl + j];
+            for (int aa = 0; aa < 2; ++aa)
+              for (int bb = 0; bb < 2; ++bb) {
+                int r = 2 * i + aa, c = 2 * j + bb;
+                if (c < r) continue;
+                double v = lam * G[aa * nnl + i] * G[bb * nnl + j] +
+                           mu * G[bb * nnl + i] * G[aa * nnl + j] + (aa == bb ? mu * gg : 0.0);
+                K[r * nl + c] += wa * v;
+                if (aa == bb) M[r * nl + c] += mc * N[i] * N[j];
+              }
+          }
+      }
+    }
+  }
+
+  static void symmetrize(int nl, double* A) {
+    for (int i = 0; i < nl; ++i)
+      for (int j = 0; j < i; ++j) A[i * nl + j] = A[j * nl + i];
+  }
+
+  // Space tree over cell `cell` with lower corner clo.
+  void cut_cell(const Geo& geo, int64_t cell, const double* clo, double* K, double* M) const {
+    const int d = s->dim;
+    const int nl = s->n_loc;
+    std::fill(K, K + nl * nl, 0.0);
+    std::fill(M, M + nl * nl, 0.0);
+    int64_t cidx[3] = {0, 0, 0};
+    int64_t rem = cell;
+    for (int k = 0; k < d; ++k) {
+      cidx[k] = rem % s->n[k];
+      rem /= s->n[k];
+    }
+    struct Node { int level; int64_t sub[3]; };
+    std::vector<Node> stack;
+    stack.push_back({0, {0, 0, 0}});
+    const int depth = in->geom.quad_depth;
+    while (!stack.empty()) {
+      Node nd = stack.back();
+      stack.pop_back();
+      int64_t scale = (int64_t)1 << nd.level;
+      double blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+      int64_t ilo[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) {
+        double hs = s->h[k] / (double)scale;
+        blo[k] = clo[k] + nd.sub[k] * hs;
+        bhi[k] = blo[k] + hs;
+        ilo[k] = cidx[k] * scale + nd.sub[k];
+      }
+      CellClass c = geo.classify(blo, bhi, ilo, scale);
+      if (c == kUncut) {
+        accumulate(geo, clo, blo, bhi, 1.0, K, M);
+      } else if (c == kOutside) {
+        accumulate(geo, clo, blo, bhi, in->alpha, K, M);
+      } else if (nd.level >= depth) {
+        accumulate(geo, clo, blo, bhi, -1.0, K, M);
+      } else {
+        // children pushed in reverse so that they are integrated in x-fastest order
+        int nch = 1 << d;
+        for (int ch = nch - 1; ch >= 0; --ch) {
+          Node c2{nd.level + 1, {0, 0, 0}};
+          for (int k = 0; k < d; ++k) c2.sub[k] = nd.sub[k] * 2 + ((ch >> k) & 1);
+          stack.push_back(c2);
+        }
+      }
+    }
+    symmetrize(nl, K);
+    symmetrize(nl, M);
+  }
+};
+
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body) {
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  int nt = (int)std::min<int64_t>(hw, std::max<int64_t>(1, n / 16));
+  if (nt <= 1) {
+    body(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::atomic<int64_t> next{0};
+  const int64_t chunk = 16;
+  std::exception_ptr err;
+  std::atomic<bool> failed{false};
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (;;) {
+        int64_t a = next.fetch_add(chunk);
+        if (a >= n || failed.load()) break;
+        try {
+          body(a, std::min(n, a + chunk));
+        } catch (...) {
+          if (!failed.exchange(true)) err = std::current_exception();
+          break;
+        }
+      }
+    });
+  for (auto& t : th) t.join();
+  if (err) std::rethrow_exception(err);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ symmetric eigen
+bool sym_eig(int n, double* A, double* evals, double* evecs) {
+  // Householder reduction to tridiagonal form T = Q^T A Q, then implicit-shift QL.
+  std::vector<double> Q(n * n, 0.0), diag(n), off(n, 0.0), v(n), pv(n);
+  for (int i = 0; i < n; ++i) Q[i * n + i] = 1.0;
+  for (int k = 0; k + 2 < n; ++k) {
+    double nrm = 0;
+    for (int i = k + 1; i < n; ++i) nrm += A[i * n + k] * A[i * n + k];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) continue;
+    double x0 = A[(k + 1) * n + k];
+    double alpha = x0 > 0 ? -nrm : nrm;
+    // v = x - alpha e1, normalised
+    for (int i = 0; i < n; ++i) v[i] = 0.0;
+    for (int i = k + 1; i < n; ++i) v[i] = A[i * n + k];
+    v[k + 1] -= alpha;
+    double vn = 0;
+    for (int i = k + 1; i < n; ++i) vn += v[i] * v[i];
+    vn = std::sqrt(vn);
+    if (vn == 0.0) continue;
+    for (int i = k + 1; i < n; ++i) v[i] /= vn;
+    // A <- H A H with H = I - 2 v v^T: A - v w^T - w v^T, w = 2 A v - 2 (v^T A v) v
+    for (int i = 0; i < n; ++i) {
+      double acc = 0;
+      for (int j = k + 1; j < n; ++j) acc += A[i * n + j] * v[j];
+      pv[i] = 2.0 * acc;
+    }
+    double vpv = 0;
+    for (int i = k + 1; i < n; ++i) vpv += v[i] * pv[i];
+    for (int i = 0; i < n; ++i) pv[i] -= vpv * v[i];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[i * n + j] -= v[i] * pv[j] + pv[i] * v[j];
+    // Q <- Q H
+    for (int i = 0; i < n; ++i) {
+      double acc = 0;
+      for (int j = k + 1; j < n; ++j) acc += Q[i * n + j] * v[j];
+      for (int j = k + 1; j < n; ++j) Q[i * n + j] -= 2.0 * acc * v[j];
+    }
+  }
+  for (int i = 0; i < n; ++i) diag[i] = A[i * n + i];
+  for (int i = 0; i + 1 < n; ++i) off[i] = A[(i + 1) * n + i];
+  off[n - 1] = 0.0;
+  // QL iterations on (diag, off); off[i] couples i and i + 1.
+  const double tiny = 2.2204460492503131e-16;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      int m = l;
+      for (; m + 1 < n; ++m) {
+        double dd = std::fabs(diag[m]) + std::fabs(diag[m + 1]);
+        if (std::fabs(off[m]) <= tiny * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 200) return false;
+      double g = (diag[l + 1] - diag[l]) / (2.0 * off[l]);
+      double r = std::hypot(g, 1.0);
+      g = diag[m] - diag[l] + off[l] / (g + (g >= 0 ? r : -r));
+      double sn = 1.0, cs = 1.0, p = 0.0;
+      bool early = false;
+      for (int i = m - 1; i >= l; --i) {
+        double f = sn * off[i], b = cs * off[i];
+        r = std::hypot(f, g);
+        off[i + 1] = r;
+        if (r == 0.0) {
+          diag[i + 1] -= p;
+          off[m] = 0.0;
+          early = true;
+          break;
+        }
+        sn = f / r;
+        cs = g / r;
+        g = diag[i + 1] - p;
+        r = (diag[i] - g) * sn + 2.0 * cs * b;
+        p = sn * r;
+        diag[i + 1] = g + p;
+        g = cs * r - b;
+        for (int k = 0; k < n; ++k) {
+          double t = Q[k * n + i + 1];
+          Q[k * n + i + 1] = sn * Q[k * n + i] + cs * t;
+          Q[k * n + i] = cs * Q[k * n + i] - sn * t;
+        }
+      }
+      if (early) continue;
+      diag[l] -= p;
+      off[l] = g;
+      off[m] = 0.0;
+    }
+  }
+  // sort ascending
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return diag[a] < diag[b]; });
+  for (int j = 0; j < n; ++j) {
+    evals[j] = diag[order[j]];
+    if (evecs)
+      for (int i = 0; i < n; ++i) evecs[i * n + j] = Q[i * n + order[j]];
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ public helpers
+int64_t lattice_node(const Setup& s, int64_t cell, int loc) {
+  int64_t rem = cell, node = 0, stride = 1;
+  int l = loc;
+  for (int k = 0; k < s.dim; ++k) {
+    int64_t ck = rem % s.n[k];
+    rem /= s.n[k];
+    int a = l % s.nn1;
+    l /= s.nn1;
+    node += (ck * s.p + a) * stride;
+    stride *= s.lat[k];
+  }
+  return node;
+}
+
+int64_t locate_cell(const Setup& s, const double* x) {
+  int64_t best = -1;
+  int64_t base[3] = {0, 0, 0};
+  for (int k = 0; k < s.dim; ++k) base[k] = (int64_t)std::floor((x[k] - s.lo[k]) / s.h[k]);
+  int ncand = 1 << s.dim;
+  for (int o = 0; o < ncand; ++o) {
+    int64_t ck[3];
+    bool ok = true;
+    for (int k = 0; k < s.dim; ++k) {
+      ck[k] = base[k] - ((o >> k) & 1);
+      if (ck[k] < 0 || ck[k] >= s.n[k]) { ok = false; break; }
+      double lo = s.lo[k] + ck[k] * s.h[k];
+      if (x[k] < lo - 1e-14 || x[k] > lo + s.h[k] + 1e-14) { ok = false; break; }
+    }
+    if (!ok) continue;
+    int64_t cell = 0, stride = 1;
+    for (int k = 0; k < s.dim; ++k) {
+      cell += ck[k] * stride;
+      stride *= s.n[k];
+    }
+    if (s.cls[cell] == kOutside) continue;
+    if (best < 0 || cell < best) best = cell;
+  }
+  return best;
+}
+
+void shape_values(const Setup& s, int64_t cell, const double* x, double* N) {
+  int64_t rem = cell;
+  std::vector<double> L(s.dim * s.nn1);
+  for (int k = 0; k < s.dim; ++k) {
+    int64_t ck = rem % s.n[k];
+    rem /= s.n[k];
+    double t = 2.0 * (x[k] - (s.lo[k] + ck * s.h[k])) / s.h[k] - 1.0;
+    lagrange1d(s.gll_x, t, &L[k * s.nn1], nullptr);
+  }
+  for (int j = 0; j < s.nn_loc; ++j) {
+    int jj = j;
+    double v = 1.0;
+    for (int k = 0; k < s.dim; ++k) {
+      v *= L[k * s.nn1 + jj % s.nn1];
+      jj /= s.nn1;
+    }
+    N[j] = v;
+  }
+}
+
+double indicator(const SetupInput& in, const double* x) {
+  Geo g(in);
+  return g.physical_point(x) ? 1.0 : in.alpha;
+}
+
+void edge_traction(const Setup& s, const SetupInput& in, double y0, double y1,
+                   const double* t, std::vector<int64_t>& dofs, std::vector<double>& vals) {
+  Geo geo(in);
+  std::vector<double> gx, gw;
+  gauss_rule(s.p + 1, gx, gw);
+  std::vector<double> L(s.nn1);
+  for (int ey = 0; ey < s.n[1]; ++ey) {
+    int64_t cell = (int64_t)ey * s.n[0];
+    if (s.cls[cell] == kOutside) continue;
+    double ylo = s.lo[1] + ey * s.h[1], yhi = ylo + s.h[1];
+    double a0 = std::max(ylo, y0), a1 = std::min(yhi, y1);
+    if (a1 <= a0) continue;
+    // only local nodes with x-index 0 are nonzero on the edge x = lo_x
+    std::vector<double> integ(s.nn1, 0.0);
+    for (size_t q = 0; q < gx.size(); ++q) {
+      double y = a0 + (gx[q] + 1.0) * 0.5 * (a1 - a0);
+      double w = gw[q] * 0.5 * (a1 - a0);
+      double xp[3] = {s.lo[0], y, 0.0};
+      double al = geo.physical_point(xp) ? 1.0 : in.alpha;
+      lagrange1d(s.gll_x, 2.0 * (y - ylo) / s.h[1] - 1.0, L.data(), nullptr);
+      for (int b = 0; b < s.nn1; ++b) integ[b] += w * al * L[b];
+    }
+    for (int b = 0; b < s.nn1; ++b) {
+      int64_t node = lattice_node(s, cell, b * s.nn1);
+      for (int c = 0; c < s.ncomp; ++c) {
+        double v = integ[b] * t[c];
+        if (v == 0.0) continue;
+        dofs.push_back(node * s.ncomp + c);
+        vals.push_back(v);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ build
+Setup build_setup(const SetupInput& in) {
+  Setup s;
+  if (in.dim != 2 && in.dim != 3) throw std::invalid_argument("dim must be 2 or 3");
+  if (in.p < 1 || in.p > 8) throw std::invalid_argument("p must be in 1..8");
+  if (in.physics == 1 && in.dim != 2) throw std::invalid_argument("plane strain needs dim 2");
+  s.dim = in.dim;
+  s.p = in.p;
+  s.ncomp = in.physics == 1 ? 2 : 1;
+  s.nn1 = in.p + 1;
+  s.nn_loc = 1;
+  for (int k = 0; k < s.dim; ++k) s.nn_loc *= s.nn1;
+  s.n_loc = s.nn_loc * s.ncomp;
+  s.n_elem = 1;
+  s.n_lat_nodes = 1;
+  for (int k = 0; k < 3; ++k) {
+    s.n[k] = k < s.dim ? in.n[k] : 1;
+    if (s.n[k] < 1) throw std::invalid_argument("cells per axis must be >= 1");
+    s.lo[k] = k < s.dim ? in.lo[k] : 0.0;
+    s.h[k] = k < s.dim ? (in.hi[k] - in.lo[k]) / in.n[k] : 1.0;
+    if (k < s.dim && !(s.h[k] > 0)) throw std::invalid_argument("empty extended box");
+    s.lat[k] = k < s.dim ? (int64_t)s.n[k] * s.p + 1 : 1;
+    s.n_elem *= s.n[k];
+    s.n_lat_nodes *= s.lat[k];
+  }
+  s.n_lat_dof = s.n_lat_nodes * s.ncomp;
+  gll_rule(s.p, s.gll_x, s.gll_w);
+  Geo geo(in);
+
+  // classification
+  s.cls.assign(s.n_elem, kUncut);
+  if (in.geom.kind != 0) {
+    parallel_for(s.n_elem, [&](int64_t a, int64_t b) {
+      for (int64_t e = a; e < b; ++e) {
+        double blo[3], bhi[3];
+        int64_t ilo[3] = {0, 0, 0}, rem = e;
+        for (int k = 0; k < s.dim; ++k) {
+          ilo[k] = rem % s.n[k];
+          rem /= s.n[k];
+          blo[k] = s.lo[k] + ilo[k] * s.h[k];
+          bhi[k] = blo[k] + s.h[k];
+        }
+        s.cls[e] = geo.classify(blo, bhi, ilo, 1);
+      }
+    });
+  }
+  s.cut_index.assign(s.n_elem, -1);
+  for (int64_t e = 0; e < s.n_elem; ++e) {
+    if (s.cls[e] == kCut) {
+      s.cut_index[e] = (int32_t)s.cut_cells.size();
+      s.cut_cells.push_back(e);
+    } else if (s.cls[e] == kUncut) {
+      ++s.n_uncut;
+    } else {
+      ++s.n_outside;
+    }
+  }
+  s.n_cut = (int64_t)s.cut_cells.size();
+  if (s.n_cut + s.n_uncut == 0) throw std::domain_error("no cell intersects the physical domain");
+
+  // node numbering: kept nodes in lattice order
+  std::vector<uint8_t> used(s.n_lat_nodes, 0);
+  for (int64_t e = 0; e < s.n_elem; ++e) {
+    if (s.cls[e] == kOutside) continue;
+    for (int l = 0; l < s.nn_loc; ++l) used[lattice_node(s, e, l)] = 1;
+  }
+  s.kept_of_lat.assign(s.n_lat_nodes, -1);
+  for (int64_t i = 0; i < s.n_lat_nodes; ++i)
+    if (used[i]) {
+      s.kept_of_lat[i] = (int64_t)s.lat_of_kept.size();
+      s.lat_of_kept.push_back(i);
+    }
+  s.n_kept_nodes = (int64_t)s.lat_of_kept.size();
+  s.n_dof = s.n_kept_nodes * s.ncomp;
+
+  // reference cell: GL stiffness, GLL lumped mass
+  ElementIntegrator integ(s, in);
+  const int nl = s.n_loc;
+  s.Kref.assign(nl * nl, 0.0);
+  std::vector<double> Mfull(nl * nl, 0.0);
+  {
+    double clo[3] = {s.lo[0], s.lo[1], s.lo[2]}, chi[3];
+    for (int k = 0; k < 3; ++k) chi[k] = clo[k] + s.h[k];
+    integ.accumulate(geo, clo, clo, chi, 1.0, s.Kref.data(), Mfull.data());
+    ElementIntegrator::symmetrize(nl, s.Kref.data());
+    ElementIntegrator::symmetrize(nl, Mfull.data());
+  }
+  s.mref.assign(nl, 0.0);
+  for (int j = 0; j < s.nn_loc; ++j) {
+    int jj = j;
+    double m = in.rho;
+    for (int k = 0; k < s.dim; ++k) {
+      m *= s.gll_w[jj % s.nn1] * 0.5 * s.h[k];
+      jj /= s.nn1;
+    }
+    for (int c = 0; c < s.ncomp; ++c) s.mref[j * s.ncomp + c] = m;
+  }
+  auto lambda_max_lumped = [&](const double* K, const double* ml) {
+    std::vector<double> A(nl * nl), ev(nl);
+    for (int i = 0; i < nl; ++i)
+      for (int j = 0; j < nl; ++j) A[i * nl + j] = K[i * nl + j] / std::sqrt(ml[i] * ml[j]);
+    if (!sym_eig(nl, A.data(), ev.data(), nullptr)) throw std::runtime_error("eigensolver failed");
+    return ev[nl - 1];
+  };
+  s.lambda_ref = lambda_max_lumped(s.Kref.data(), s.mref.data());
+  double mfull_max = *std::max_element(Mfull.begin(), Mfull.end());
+
+  // cut cells
+  s.Kcut.assign((size_t)s.n_cut * nl * nl, 0.0);
+  s.mlcut.assign((size_t)s.n_cut * nl, 0.0);
+  if (in.need_consistent_mass) s.Mcut.assign((size_t)s.n_cut * nl * nl, 0.0);
+  parallel_for(s.n_cut, [&](int64_t a, int64_t b) {
+    std::vector<double> M(nl * nl), Ms(nl * nl), V(nl * nl), ev(nl);
+    for (int64_t ci = a; ci < b; ++ci) {
+      int64_t e = s.cut_cells[ci];
+      double clo[3] = {0, 0, 0};
+      int64_t rem = e;
+      for (int k = 0; k < s.dim; ++k) {
+        clo[k] = s.lo[k] + (rem % s.n[k]) * s.h[k];
+        rem /= s.n[k];
+      }
+      double* K = &s.Kcut[(size_t)ci * nl * nl];
+      integ.cut_cell(geo, e, clo, K, M.data());
+      if (in.need_consistent_mass) std::copy(M.begin(), M.end(), &s.Mcut[(size_t)ci * nl * nl]);
+      // eigenvalue stabilisation M^e = M^o + eps M^s (Eq. epsilon_stabilization)
+      if (in.stab == 1) {
+        std::copy(M.begin(), M.end(), Ms.begin());
+        if (!sym_eig(nl, Ms.data(), ev.data(), V.data())) throw std::runtime_error("EVS eigensolver failed");
+        double thr = in.f_lambda * ev[nl - 1];
+        std::fill(Ms.begin(), Ms.end(), 0.0);
+        bool any = false;
+        for (int j = 0; j < nl; ++j) {
+          if (!(ev[j] < thr)) continue;
+          any = true;
+          for (int r = 0; r < nl; ++r) {
+            double vr = V[r * nl + j];
+            for (int c = 0; c < nl; ++c) Ms[r * nl + c] += vr * V[c * nl + j];
+          }
+        }
+        if (any) {
+          double mx = *std::max_element(Ms.begin(), Ms.end());
+          double sc = in.eps * mfull_max / mx;
+          for (int i = 0; i < nl * nl; ++i) M[i] += sc * Ms[i];
+        }
+      }
+      // HRZ lumping: diagonal scaled to the element's total mass
+      double total = 0, tr = 0;
+      for (int i = 0; i < nl * nl; ++i) total += M[i];
+      for (int i = 0; i < nl; ++i) tr += M[i * nl + i];
+      double* ml = &s.mlcut[(size_t)ci * nl];
+      for (int i = 0; i < nl; ++i) ml[i] = total * M[i * nl + i] / tr;
+      if (in.stab == 2) {
+        double lam = lambda_max_lumped(K, ml);
+        double sc = std::max(1.0, lam / s.lambda_ref);
+        for (int i = 0; i < nl; ++i) ml[i] *= sc;
+      }
+    }
+  });
+
+  // assembled lumped mass on the lattice
+  s.ML.assign(s.n_lat_dof, 0.0);
+  for (int64_t e = 0; e < s.n_elem; ++e) {
+    if (s.cls[e] == kOutside) continue;
+    const double* ml = s.cls[e] == kCut ? &s.mlcut[(size_t)s.cut_index[e] * nl] : s.mref.data();
+    for (int l = 0; l < s.nn_loc; ++l) {
+      int64_t node = lattice_node(s, e, l);
+      for (int c = 0; c < s.ncomp; ++c) s.ML[node * s.ncomp + c] += ml[l * s.ncomp + c];
+    }
+  }
+  return s;
+}
+
+}  // namespace ibfem

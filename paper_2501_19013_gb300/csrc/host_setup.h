@@ -1,0 +1,112 @@
+// Host-side construction of the spectral-cell discretisation (library side).
+//
+// Everything here runs once per problem, before any time step: cell classification,
+// space-tree quadrature of cut cells, element matrices with the finite cell indicator,
+// eigenvalue stabilisation, HRZ lumping, mass scaling, the lumped mass on the node
+// lattice, loads, observers and the IMEX partition with its Cholesky factor.  The
+// result is a set of flat arrays in the device layout (node lattice, x fastest,
+// components interleaved) that the runtime uploads.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ibfem {
+
+enum CellClass : uint8_t { kOutside = 0, kCut = 1, kUncut = 2 };
+
+struct GeometryDesc {
+  int kind = 0;                 // IBFEM_GEOM_*
+  std::vector<double> shapes;   // holes: (c..., r); rotated box: (edge, c[3], T[9])
+  std::vector<uint8_t> voxels;  // x fastest
+  int vn[3] = {1, 1, 1};
+  int quad_depth = 0;
+};
+
+struct SetupInput {
+  int dim = 2;
+  int n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  int p = 2;
+  int physics = 0;  // 0 scalar, 1 plane strain
+  double rho = 1, c = 1, E = 1, nu = 0.3;
+  double alpha = 1e-5;
+  int stab = 0;     // 0 none, 1 EVS, 2 mass scaling
+  double eps = 0, f_lambda = 1e-2;
+  GeometryDesc geom;
+  bool need_consistent_mass = false;  // IMEX: keep the consistent cut mass
+};
+
+struct Setup {
+  // grid
+  int dim = 2, p = 2, ncomp = 1, nn1 = 3, nn_loc = 9, n_loc = 9;
+  int n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  int64_t lat[3] = {1, 1, 1};   // lattice nodes per axis
+  int64_t n_lat_nodes = 0, n_lat_dof = 0, n_elem = 0;
+  // classification
+  std::vector<uint8_t> cls;          // per cell
+  std::vector<int32_t> cut_index;    // per cell, -1 unless cut
+  std::vector<int64_t> cut_cells;    // cut index -> cell
+  int64_t n_uncut = 0, n_cut = 0, n_outside = 0;
+  // numbering
+  std::vector<int64_t> kept_of_lat;  // lattice node -> kept node or -1
+  std::vector<int64_t> lat_of_kept;  // kept node -> lattice node
+  int64_t n_kept_nodes = 0, n_dof = 0;
+  // matrices
+  std::vector<double> Kref;          // n_loc^2
+  std::vector<double> mref;          // n_loc, GLL lumped
+  double lambda_ref = 0;
+  std::vector<double> Kcut;          // n_cut * n_loc^2, row-major, symmetric
+  std::vector<double> Mcut;          // n_cut * n_loc^2 consistent (alpha) mass (if kept)
+  std::vector<double> mlcut;         // n_cut * n_loc lumped (HRZ [+EVS] [x scale])
+  std::vector<double> ML;            // lattice dof -> assembled lumped mass (0 = dead)
+  // 1D GLL data
+  std::vector<double> gll_x, gll_w;
+};
+
+// Throws std::runtime_error with a message on failure; `code` receives an IBFEM_ERR_*.
+Setup build_setup(const SetupInput& in);
+
+// Shape functions of cell `cell` at physical point x: writes nn_loc values.
+void shape_values(const Setup& s, int64_t cell, const double* x, double* N);
+
+// Cell containing x (lowest kept index among the closed boxes), or -1.
+int64_t locate_cell(const Setup& s, const double* x);
+
+// Lattice node index of local node `loc` of `cell`.
+int64_t lattice_node(const Setup& s, int64_t cell, int loc);
+
+// alpha^FCM at a point (1 inside the physical domain).
+double indicator(const SetupInput& in, const double* x);
+
+// Edge-traction load on x = lo_x, y in [y0, y1]: returns (lattice dof, value) pairs.
+void edge_traction(const Setup& s, const SetupInput& in, double y0, double y1,
+                   const double* t, std::vector<int64_t>& dofs, std::vector<double>& vals);
+
+// Symmetric eigen-decomposition (Householder tridiagonalisation + implicit QL).
+// A is n x n row-major (destroyed); evals ascending; evecs (row-major, column j =
+// eigenvector j) if non-null.  Returns false if QL fails to converge.
+bool sym_eig(int n, double* A, double* evals, double* evecs);
+
+// Simplicial sparse Cholesky of a symmetric positive definite CSR matrix (full pattern)
+// after the given symmetric permutation.  Produces L in CSR (rows, strictly lower part
+// plus diagonal last in each row) and level sets for the forward solve.
+struct SparseChol {
+  int64_t n = 0;
+  std::vector<int64_t> Lp, Li;       // CSR of L (lower), diagonal stored last per row
+  std::vector<double> Lx;
+  std::vector<int64_t> Up, Ui;       // CSR of L^T (upper), diagonal first per row
+  std::vector<double> Ux;
+  std::vector<int32_t> fwd_level_ptr, fwd_rows;  // level schedule of L y = b
+  std::vector<int32_t> bwd_level_ptr, bwd_rows;  // level schedule of L^T x = y
+};
+bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
+                     const std::vector<double>& Ax, SparseChol& out, std::string& err);
+
+// Reverse Cuthill-McKee ordering of a symmetric pattern; perm[new] = old.
+std::vector<int64_t> rcm_order(int64_t n, const std::vector<int64_t>& Ap,
+                               const std::vector<int64_t>& Ai);
+
+}  // namespace ibfem

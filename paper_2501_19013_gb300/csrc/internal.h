@@ -1,0 +1,72 @@
+// Internal device-side types shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ibfem {
+
+// Per-lattice-DOF arrays use the node lattice (n_k p + 1 nodes per axis, x fastest) with
+// the ncomp components of a node interleaved.  Dead lattice nodes (not in any kept cell)
+// carry zero mass and are never written.
+struct DevProblem {
+  int dim, p, ncomp, n_loc, nn_loc;
+  int n[3];          // cells per axis
+  int lat[3];        // lattice nodes per axis
+  int64_t n_lat_dof;
+  const uint8_t* cls;       // per cell: 0 outside, 1 cut, 2 uncut
+  const int32_t* cut_index; // per cell
+  const int64_t* cut_cell;  // cut index -> cell
+  int n_cut;
+  const double* Kref;       // n_loc^2 (symmetric)
+  const double* Kcut;       // n_cut * n_loc^2 (symmetric, row-major)
+  const float* Kcut32;      // same in FP32 (mixed precision), may be null
+  double* Ycut;             // n_cut * n_loc: K^e x_e of the cut cells for the current step
+  const double* minv;       // dt^2 / M_L per lattice DOF (0 = dead); -(c + 1) marks IMEX c-DOF c
+  const double* sinv;       // 1 / sqrt(M_L) per lattice DOF (0 = dead or IMEX c-DOF)
+  // source: per tile CSR of (lattice dof, value)
+  const int32_t* src_ptr;   // n_tiles + 1, or null
+  const int64_t* src_dof;
+  const double* src_val;
+  double f_e;               // Ricker centre frequency (0 = no source)
+  double dt;
+  // observers
+  int n_obs_rows;           // observers x ncomp
+  int obs_nodes;            // nn_loc
+  const int64_t* obs_dof;   // n_obs_rows * nn_loc lattice dofs
+  const double* obs_w;      // n_obs_rows * nn_loc weights
+  double* ring;             // capacity * n_obs_rows
+  int64_t ring_cap;
+  // counters
+  unsigned long long* step; // device step counter
+  unsigned int* done;       // block-completion counter for the step increment
+  int* flags;               // bit 0: non-finite state
+  int tiles[3];             // tile grid of the fused kernel
+};
+
+// Input transform of the operator kernels: x_i = in[i] * (vec ? vec[i] : 1) * (scal ? *scal : 1)
+struct OpInput {
+  const double* in;
+  const double* vec;
+  const double* scal;
+};
+
+enum OpMode : int {
+  kModeCDM = 0,       // out <- 2u - out + minv (F_k - K u), u = the input
+  kModeStartup = 1,   // out <- u - dt * out + 0.5 minv (F_0 - K u)  (out holds v0)
+  kModeApply = 2,     // out <- K x
+  kModePower = 3,     // out <- sinv * K x, partial sums of x_in * out and out * out
+};
+
+// Launchers (kernels_fp64.cu)
+cudaError_t launch_cut_apply_fp64(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st);
+cudaError_t launch_op_fp64(const DevProblem& pb, OpInput x, double* out, int mode,
+                           double* partials, cudaStream_t st);
+cudaError_t launch_reduce_power(const double* partials, int nblocks, double* lam_hist,
+                                double* inv_norm, int iter, cudaStream_t st);
+cudaError_t launch_sample_now(const DevProblem& pb, const double* u, double* out, cudaStream_t st);
+int op_fp64_blocks(const DevProblem& pb);
+bool op_fp64_supported(int dim, int p, int ncomp);
+void op_fp64_tiles(int dim, int p, int ncomp, int* tile);
+
+}  // namespace ibfem

@@ -1,0 +1,753 @@
+// C ABI runtime: handle, device buffers, CUDA-graph replay of the per-step kernels.
+//
+// The public functions are declared and documented in include/ibfem.h.  The time step
+// is Eq. cdm of Buerchner et al. (arXiv 2501.19013); the critical step follows Sec. 2.3.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ibfem.h"
+#include "host_setup.h"
+#include "internal.h"
+#include "runtime_internal.h"
+
+using namespace ibfem;
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct CudaFail : std::runtime_error {
+  explicit CudaFail(const std::string& m) : std::runtime_error(m) {}
+};
+
+void check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw CudaFail(std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace
+
+namespace ibfem {
+
+void* Handle::dalloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (opt.dev_alloc) {
+    p = opt.dev_alloc(bytes, opt.alloc_ctx);
+    if (!p) throw std::bad_alloc();
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+  }
+  allocs.push_back(p);
+  device_bytes += bytes;
+  return p;
+}
+
+void Handle::dfree_all() {
+  for (void* p : allocs) {
+    if (opt.dev_free) opt.dev_free(p, opt.alloc_ctx);
+    else cudaFree(p);
+  }
+  allocs.clear();
+  device_bytes = 0;
+}
+
+template <typename T>
+T* Handle::upload(const std::vector<T>& v) {
+  T* d = static_cast<T*>(dalloc(std::max<size_t>(v.size(), 1) * sizeof(T)));
+  if (!v.empty()) check(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream), "upload");
+  return d;
+}
+
+void Handle::to_lattice(const double* kept, std::vector<double>& lat) const {
+  lat.assign(setup.n_lat_dof, 0.0);
+  if (!kept) return;
+  const int nc = setup.ncomp;
+  for (int64_t i = 0; i < setup.n_kept_nodes; ++i)
+    for (int c = 0; c < nc; ++c) lat[setup.lat_of_kept[i] * nc + c] = kept[i * nc + c];
+}
+
+void Handle::from_lattice(const std::vector<double>& lat, double* kept) const {
+  const int nc = setup.ncomp;
+  for (int64_t i = 0; i < setup.n_kept_nodes; ++i)
+    for (int c = 0; c < nc; ++c) kept[i * nc + c] = lat[setup.lat_of_kept[i] * nc + c];
+}
+
+void Handle::build_device() {
+  const Setup& s = setup;
+  DevProblem& pb = dev;
+  std::memset(&pb, 0, sizeof(pb));
+  pb.dim = s.dim;
+  pb.p = s.p;
+  pb.ncomp = s.ncomp;
+  pb.n_loc = s.n_loc;
+  pb.nn_loc = s.nn_loc;
+  for (int k = 0; k < 3; ++k) {
+    pb.n[k] = s.n[k];
+    pb.lat[k] = (int)s.lat[k];
+  }
+  pb.n_lat_dof = s.n_lat_dof;
+  pb.cls = upload(s.cls);
+  pb.cut_index = upload(s.cut_index);
+  pb.cut_cell = upload(s.cut_cells);
+  pb.n_cut = (int)s.n_cut;
+  pb.Kref = upload(s.Kref);
+  pb.Kcut = upload(s.Kcut);
+  pb.Ycut = static_cast<double*>(dalloc(std::max<int64_t>(s.n_cut, 1) * s.n_loc * sizeof(double)));
+  // 1/M_L (dt = 1 until set_dt) and 1/sqrt(M_L)
+  std::vector<double> minv(s.n_lat_dof, 0.0), sinv(s.n_lat_dof, 0.0);
+  for (int64_t i = 0; i < s.n_lat_dof; ++i)
+    if (s.ML[i] > 0) {
+      minv[i] = 1.0 / s.ML[i];
+      sinv[i] = 1.0 / std::sqrt(s.ML[i]);
+    }
+  d_minv = upload(minv);
+  pb.minv = d_minv;
+  pb.sinv = upload(sinv);
+  for (int b = 0; b < 2; ++b) {
+    U[b] = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+    check(cudaMemsetAsync(U[b], 0, s.n_lat_dof * sizeof(double), stream), "memset");
+  }
+  W = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+  check(cudaMemsetAsync(W, 0, s.n_lat_dof * sizeof(double), stream), "memset");
+  counters = static_cast<unsigned long long*>(dalloc(4 * sizeof(unsigned long long)));
+  check(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), stream), "memset");
+  pb.step = counters;
+  pb.done = reinterpret_cast<unsigned int*>(counters + 1);
+  pb.flags = reinterpret_cast<int*>(counters + 2);
+  op_fp64_tiles(s.dim, s.p, s.ncomp, tile);
+  for (int k = 0; k < 3; ++k) pb.tiles[k] = k < s.dim ? (s.n[k] + tile[k] - 1) / tile[k] : 1;
+  n_blocks = op_fp64_blocks(pb);
+  partials = static_cast<double*>(dalloc(2 * (size_t)n_blocks * sizeof(double)));
+  scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
+  lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
+  scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+  check(cudaStreamSynchronize(stream), "setup sync");
+}
+
+void Handle::invalidate_graphs() {
+  for (auto& g : graphs) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+void Handle::timed_begin(int slot) {
+  if (!timing) return;
+  while (ev_pool.size() < ev_used + 2) {
+    cudaEvent_t e;
+    check(cudaEventCreate(&e), "event");
+    ev_pool.push_back(e);
+  }
+  check(cudaEventRecord(ev_pool[ev_used], stream), "event record");
+  ev_slot.push_back(slot);
+  n_slots = std::max(n_slots, slot + 1);
+}
+
+void Handle::timed_end() {
+  if (!timing) return;
+  check(cudaEventRecord(ev_pool[ev_used + 1], stream), "event record");
+  ev_used += 2;
+}
+
+void Handle::timed_collect() {
+  check(cudaStreamSynchronize(stream), "timed sync");
+  for (size_t i = 0; i < ev_slot.size(); ++i) {
+    float ms = 0.f;
+    check(cudaEventElapsedTime(&ms, ev_pool[2 * i], ev_pool[2 * i + 1]), "elapsed");
+    slot_ms[ev_slot[i]] += ms;
+  }
+  ev_slot.clear();
+  ev_used = 0;
+}
+
+// One CDM step with u = U[cur], out = U[1 - cur] (in place over u^{k-1}).
+void Handle::enqueue_step(int cur) {
+  OpInput x{U[cur], nullptr, nullptr};
+  slot_name[0] = "cut_apply_fp64";
+  slot_name[1] = "op_fp64_fused_cdm";
+  timed_begin(0);
+  check(launch_cut_apply_fp64(dev, x, true, stream), "cut_apply");
+  timed_end();
+  timed_begin(1);
+  check(launch_op_fp64(dev, x, U[1 - cur], kModeCDM, nullptr, stream), "op_fused");
+  timed_end();
+}
+
+void Handle::run_steps(int64_t n) {
+  if (n <= 0) return;
+  int64_t done_n = 0;
+  // align to even parity so that the captured chunk starts with U[0] as u^k
+  while (done_n < n && (cur != 0 || n - done_n < kGraphSteps)) {
+    enqueue_step(cur);
+    cur ^= 1;
+    ++done_n;
+  }
+  while (n - done_n >= kGraphSteps) {
+    if (!graphs[0]) {
+      cudaGraph_t g;
+      check(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      int c = 0;
+      for (int i = 0; i < kGraphSteps; ++i) {
+        enqueue_step(c);
+        c ^= 1;
+      }
+      check(cudaStreamEndCapture(stream, &g), "end capture");
+      cudaError_t e = cudaGraphInstantiate(&graphs[0], g, 0);
+      cudaGraphDestroy(g);
+      check(e, "graph instantiate");
+    }
+    check(cudaGraphLaunch(graphs[0], stream), "graph launch");
+    done_n += kGraphSteps;  // kGraphSteps is even: parity unchanged
+  }
+  while (done_n < n) {
+    enqueue_step(cur);
+    cur ^= 1;
+    ++done_n;
+  }
+}
+
+}  // namespace ibfem
+
+// ====================================================================== C ABI
+#define IBFEM_TRY try {
+#define IBFEM_CATCH                                                          \
+  }                                                                          \
+  catch (const CudaFail& e) { return fail(IBFEM_ERR_CUDA, e.what()); }      \
+  catch (const std::bad_alloc&) { return fail(IBFEM_ERR_OOM, "allocation failed"); } \
+  catch (const std::invalid_argument& e) { return fail(IBFEM_ERR_ARG, e.what()); } \
+  catch (const std::domain_error& e) { return fail(IBFEM_ERR_GEOMETRY, e.what()); } \
+  catch (const std::exception& e) { return fail(IBFEM_ERR_EIG, e.what()); }
+
+extern "C" {
+
+const char* ibfem_last_error(void) { return g_last_error.c_str(); }
+
+int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, double alpha,
+                 const ibfem_stab* stab, const ibfem_options* opt, ibfem_t** out) {
+  if (!grid || !out) return fail(IBFEM_ERR_ARG, "grid and out are required");
+  *out = nullptr;
+  std::unique_ptr<ibfem_t> h(new ibfem_t());
+  IBFEM_TRY
+  ibfem_options o{};
+  o.physics = IBFEM_SCALAR;
+  o.rho = 1.0;
+  o.c = 1.0;
+  o.E = 1.0;
+  o.nu = 0.3;
+  if (opt) o = *opt;
+  h->opt = o;
+  SetupInput& in = h->input;
+  in.dim = grid->dim;
+  for (int k = 0; k < 3; ++k) {
+    in.n[k] = grid->n[k];
+    in.lo[k] = grid->lo[k];
+    in.hi[k] = grid->hi[k];
+  }
+  in.p = p;
+  in.physics = o.physics;
+  in.rho = o.rho;
+  in.c = o.c;
+  in.E = o.E;
+  in.nu = o.nu;
+  in.alpha = alpha;
+  if (!(alpha >= 0.0)) throw std::invalid_argument("alpha must be >= 0");
+  if (o.physics != IBFEM_SCALAR && o.physics != IBFEM_ELASTIC_PLANE_STRAIN)
+    throw std::invalid_argument("unknown physics");
+  if (o.scheme != IBFEM_CDM) throw std::invalid_argument("scheme not supported by this build");
+  if (o.precision != IBFEM_FP64) throw std::invalid_argument("precision not supported by this build");
+  if (!(o.rho > 0)) throw std::invalid_argument("rho must be > 0");
+  if (stab) {
+    in.stab = stab->kind;
+    in.eps = stab->eps;
+    in.f_lambda = stab->f_lambda;
+    if (in.stab < 0 || in.stab > 2) throw std::invalid_argument("unknown stabilisation");
+  }
+  if (geometry) {
+    GeometryDesc& g = in.geom;
+    g.kind = geometry->kind;
+    g.quad_depth = geometry->quad_depth;
+    if (g.quad_depth < 0 || g.quad_depth > 12) throw std::invalid_argument("quad_depth out of range");
+    if (g.kind == IBFEM_GEOM_HOLES) {
+      if (geometry->count < 0 || (geometry->count > 0 && !geometry->shapes))
+        throw std::invalid_argument("holes need shapes");
+      g.shapes.assign(geometry->shapes, geometry->shapes + (size_t)geometry->count * (grid->dim + 1));
+    } else if (g.kind == IBFEM_GEOM_VOXELS) {
+      size_t nv = 1;
+      for (int k = 0; k < grid->dim; ++k) {
+        if (geometry->vn[k] < 1) throw std::invalid_argument("voxel counts must be >= 1");
+        g.vn[k] = geometry->vn[k];
+        nv *= (size_t)geometry->vn[k];
+      }
+      if (!geometry->voxels) throw std::invalid_argument("voxel image missing");
+      g.voxels.assign(geometry->voxels, geometry->voxels + nv);
+    } else if (g.kind == IBFEM_GEOM_ROTATED_BOX) {
+      if (grid->dim != 3 || !geometry->shapes) throw std::invalid_argument("rotated box needs dim 3 and shapes");
+      g.shapes.assign(geometry->shapes, geometry->shapes + 13);
+    } else if (g.kind != IBFEM_GEOM_NONE) {
+      throw std::invalid_argument("unknown geometry kind");
+    }
+  }
+  if (!o.host_only && !op_fp64_supported(in.dim, in.p, in.physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1))
+    throw std::invalid_argument("no kernel instantiation for this (dim, p, ncomp)");
+  h->setup = build_setup(in);
+  if (!o.host_only) {
+    check(cudaSetDevice(o.device), "cudaSetDevice");
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    if (!h->stream) {
+      // graphs cannot be captured on the legacy stream: use a private one
+      check(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+      h->own_stream = true;
+    }
+    h->build_device();
+  }
+  *out = h.release();
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_destroy(ibfem_t* h) {
+  if (!h) return IBFEM_OK;
+  if (!h->opt.host_only) {
+    cudaSetDevice(h->opt.device);
+    cudaStreamSynchronize(h->stream);
+    h->invalidate_graphs();
+    h->dfree_all();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+  }
+  delete h;
+  return IBFEM_OK;
+}
+
+int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
+  if (!h || !out) return fail(IBFEM_ERR_ARG, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  const Setup& s = h->setup;
+  out->n_dof = s.n_dof;
+  out->n_lattice_dof = s.n_lat_dof;
+  out->n_elem = s.n_elem;
+  out->n_uncut = s.n_uncut;
+  out->n_cut = s.n_cut;
+  out->n_outside = s.n_outside;
+  out->n_loc = s.n_loc;
+  out->ncomp = s.ncomp;
+  out->precision = h->opt.precision;
+  out->step = h->step;
+  out->dt = h->dt;
+  out->t = h->step * h->dt;
+  out->lambda_ref = s.lambda_ref;
+  out->device_bytes = h->device_bytes;
+  return IBFEM_OK;
+}
+
+static int require_device(ibfem_t* h) {
+  if (!h) return fail(IBFEM_ERR_ARG, "null handle");
+  if (h->opt.host_only) return fail(IBFEM_ERR_STATE, "handle was created host_only");
+  cudaError_t e = cudaSetDevice(h->opt.device);
+  if (e != cudaSuccess) return fail(IBFEM_ERR_CUDA, cudaGetErrorString(e));
+  return IBFEM_OK;
+}
+
+int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, double f_e) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  IBFEM_TRY
+  const Setup& s = h->setup;
+  std::vector<int64_t> dofs;
+  std::vector<double> vals;
+  if (kind == IBFEM_SRC_NONE) {
+    // nothing
+  } else if (kind == IBFEM_SRC_POINT) {
+    if (!params || nparams < s.dim) throw std::invalid_argument("point source needs coordinates");
+    double x[3] = {0, 0, 0};
+    for (int k = 0; k < s.dim; ++k) x[k] = params[k];
+    int64_t cell = locate_cell(s, x);
+    if (cell < 0) throw std::domain_error("point source outside the kept cells");
+    double dir[2] = {1.0, 0.0};
+    if (s.ncomp == 2 && nparams >= s.dim + 2) {
+      dir[0] = params[s.dim];
+      dir[1] = params[s.dim + 1];
+    }
+    std::vector<double> N(s.nn_loc);
+    shape_values(s, cell, x, N.data());
+    double a = indicator(h->input, x) * h->input.rho;
+    for (int l = 0; l < s.nn_loc; ++l)
+      for (int c = 0; c < s.ncomp; ++c) {
+        double v = a * N[l] * (s.ncomp == 2 ? dir[c] : 1.0);
+        if (v == 0.0) continue;
+        dofs.push_back(lattice_node(s, cell, l) * s.ncomp + c);
+        vals.push_back(v);
+      }
+  } else if (kind == IBFEM_SRC_EDGE_TRACTION) {
+    if (s.dim != 2 || !params || nparams < 3) throw std::invalid_argument("edge traction needs (y0, y1, t_x[, t_y]) in 2D");
+    double t[2] = {params[2], nparams >= 4 ? params[3] : 0.0};
+    edge_traction(s, h->input, params[0], params[1], t, dofs, vals);
+  } else {
+    throw std::invalid_argument("unknown source kind");
+  }
+  if (kind != IBFEM_SRC_NONE && !(f_e > 0)) throw std::invalid_argument("f_e must be > 0");
+  // merge duplicates and bucket by owning tile
+  std::vector<std::pair<int64_t, double>> ent;
+  for (size_t i = 0; i < dofs.size(); ++i) ent.push_back({dofs[i], vals[i]});
+  std::sort(ent.begin(), ent.end());
+  std::vector<std::pair<int64_t, double>> merged;
+  for (auto& e : ent) {
+    if (!merged.empty() && merged.back().first == e.first) merged.back().second += e.second;
+    else merged.push_back(e);
+  }
+  int ntiles = h->n_blocks;
+  std::vector<std::vector<std::pair<int64_t, double>>> per(ntiles);
+  for (auto& e : merged) {
+    int64_t node = e.first / s.ncomp;
+    int64_t rem = node;
+    int t = 0, stride = 1;
+    for (int k = 0; k < s.dim; ++k) {
+      int64_t g = rem % s.lat[k];
+      rem /= s.lat[k];
+      int b = (int)std::min<int64_t>(g / ((int64_t)h->tile[k] * s.p), h->dev.tiles[k] - 1);
+      t += b * stride;
+      stride *= h->dev.tiles[k];
+    }
+    per[t].push_back(e);
+  }
+  std::vector<int32_t> ptr(ntiles + 1, 0);
+  std::vector<int64_t> sd;
+  std::vector<double> sv;
+  for (int t = 0; t < ntiles; ++t) {
+    for (auto& e : per[t]) {
+      sd.push_back(e.first);
+      sv.push_back(e.second);
+    }
+    ptr[t + 1] = (int32_t)sd.size();
+  }
+  h->dev.src_ptr = h->upload(ptr);
+  h->dev.src_dof = h->upload(sd);
+  h->dev.src_val = h->upload(sv);
+  h->dev.f_e = kind == IBFEM_SRC_NONE ? 0.0 : f_e;
+  h->invalidate_graphs();
+  check(cudaStreamSynchronize(h->stream), "source upload");
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_set_observers(ibfem_t* h, int npts, const double* xyz, int64_t capacity) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  IBFEM_TRY
+  const Setup& s = h->setup;
+  if (npts < 0 || (npts > 0 && !xyz) || capacity < 0) throw std::invalid_argument("bad observers");
+  std::vector<int64_t> od;
+  std::vector<double> ow;
+  std::vector<double> N(s.nn_loc);
+  for (int o = 0; o < npts; ++o) {
+    double x[3] = {0, 0, 0};
+    for (int k = 0; k < s.dim; ++k) x[k] = xyz[o * s.dim + k];
+    int64_t cell = locate_cell(s, x);
+    if (cell < 0) throw std::domain_error("observer outside the kept cells");
+    shape_values(s, cell, x, N.data());
+    for (int c = 0; c < s.ncomp; ++c)
+      for (int l = 0; l < s.nn_loc; ++l) {
+        od.push_back(lattice_node(s, cell, l) * s.ncomp + c);
+        ow.push_back(N[l]);
+      }
+  }
+  h->dev.n_obs_rows = npts * s.ncomp;
+  h->dev.obs_nodes = s.nn_loc;
+  h->dev.obs_dof = h->upload(od);
+  h->dev.obs_w = h->upload(ow);
+  h->dev.ring_cap = capacity;
+  h->dev.ring = static_cast<double*>(h->dalloc(std::max<int64_t>(capacity, 1) * std::max(h->dev.n_obs_rows, 1) * sizeof(double)));
+  h->obs_out = static_cast<double*>(h->dalloc(std::max(h->dev.n_obs_rows, 1) * sizeof(double)));
+  h->ring_start = h->step;
+  h->invalidate_graphs();
+  check(cudaStreamSynchronize(h->stream), "observer upload");
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_set_dt(ibfem_t* h, double dt) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(IBFEM_ERR_ARG, "dt must be positive");
+  IBFEM_TRY
+  const Setup& s = h->setup;
+  std::vector<double> minv(s.n_lat_dof, 0.0);
+  for (int64_t i = 0; i < s.n_lat_dof; ++i)
+    if (s.ML[i] > 0) minv[i] = dt * dt / s.ML[i];
+  check(cudaMemcpyAsync(h->d_minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "minv");
+  check(cudaStreamSynchronize(h->stream), "set_dt");
+  h->dt = dt;
+  h->dev.dt = dt;
+  h->have_dt = true;
+  h->invalidate_graphs();
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_set_initial(ibfem_t* h, const double* u0, const double* v0) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (!h->have_dt) return fail(IBFEM_ERR_STATE, "set_dt before set_initial");
+  IBFEM_TRY
+  std::vector<double> lu, lv;
+  h->to_lattice(u0, lu);
+  h->to_lattice(v0, lv);
+  h->cur = 0;
+  check(cudaMemcpyAsync(h->U[0], lu.data(), lu.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "u0");
+  check(cudaMemcpyAsync(h->U[1], lv.data(), lv.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "v0");
+  check(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream), "counters");
+  OpInput x{h->U[0], nullptr, nullptr};
+  check(launch_cut_apply_fp64(h->dev, x, false, h->stream), "cut_apply");
+  check(launch_op_fp64(h->dev, x, h->U[1], kModeStartup, nullptr, h->stream), "startup");
+  check(cudaStreamSynchronize(h->stream), "set_initial");
+  h->step = 0;
+  h->ring_start = 0;
+  h->have_init = true;
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_step(ibfem_t* h, int64_t n) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (n < 0) return fail(IBFEM_ERR_ARG, "n must be >= 0");
+  if (!h->have_init) return fail(IBFEM_ERR_STATE, "set_initial (or set_state) before step");
+  IBFEM_TRY
+  h->run_steps(n);
+  h->step += n;
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_step_timed(ibfem_t* h, int64_t n, double* ms, int max_slots, int* n_slots) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (n < 0 || (max_slots > 0 && !ms)) return fail(IBFEM_ERR_ARG, "bad arguments");
+  if (!h->have_init) return fail(IBFEM_ERR_STATE, "set_initial (or set_state) before step");
+  IBFEM_TRY
+  for (double& v : h->slot_ms) v = 0.0;
+  h->timing = true;
+  for (int64_t i = 0; i < n; ++i) {
+    h->enqueue_step(h->cur);
+    h->cur ^= 1;
+    if (h->ev_used > 512) h->timed_collect();
+  }
+  h->timed_collect();
+  h->timing = false;
+  h->step += n;
+  for (int i = 0; i < std::min(max_slots, h->n_slots); ++i) ms[i] = h->slot_ms[i];
+  if (n_slots) *n_slots = h->n_slots;
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+const char* ibfem_kernel_name(const ibfem_t* h, int slot) {
+  if (!h || slot < 0 || slot >= 8) return "";
+  return h->slot_name[slot];
+}
+
+int ibfem_sync(ibfem_t* h) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  IBFEM_TRY
+  check(cudaStreamSynchronize(h->stream), "sync");
+  int flags = 0;
+  check(cudaMemcpy(&flags, h->dev.flags, sizeof(int), cudaMemcpyDeviceToHost), "flags");
+  if (flags & 1) return fail(IBFEM_ERR_DIVERGED, "non-finite value in the state");
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_sample(ibfem_t* h, int64_t max_rows, double* out, int64_t* rows) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (!out || !rows || max_rows < 0) return fail(IBFEM_ERR_ARG, "bad output");
+  IBFEM_TRY
+  const int nr = h->dev.n_obs_rows;
+  check(cudaStreamSynchronize(h->stream), "sync");
+  int64_t cap = h->dev.ring_cap;
+  int64_t first = std::max<int64_t>(h->ring_start, h->step - cap);
+  int64_t nrec = h->step - first;  // rows in the ring
+  int64_t total = nrec + 1;        // plus the current state
+  int64_t take = std::min(total, max_rows);
+  std::vector<double> ring((size_t)std::max<int64_t>(cap, 1) * std::max(nr, 1));
+  if (nr > 0 && cap > 0)
+    check(cudaMemcpy(ring.data(), h->dev.ring, (size_t)cap * nr * sizeof(double), cudaMemcpyDeviceToHost), "ring");
+  int64_t r = 0;
+  for (int64_t k = first; k < h->step && r < take; ++k, ++r)
+    std::memcpy(out + r * nr, ring.data() + (size_t)(k % cap) * nr, nr * sizeof(double));
+  if (r < take && nr > 0) {
+    check(launch_sample_now(h->dev, h->U[h->cur], h->obs_out, h->stream), "sample_now");
+    check(cudaMemcpyAsync(out + r * nr, h->obs_out, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "sample");
+    check(cudaStreamSynchronize(h->stream), "sample sync");
+    ++r;
+  }
+  *rows = r;
+  int flags = 0;
+  check(cudaMemcpy(&flags, h->dev.flags, sizeof(int), cudaMemcpyDeviceToHost), "flags");
+  if (flags & 1) return fail(IBFEM_ERR_DIVERGED, "non-finite value in the state");
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_get_state(ibfem_t* h, double* u, double* u_prev) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  IBFEM_TRY
+  const Setup& s = h->setup;
+  std::vector<double> lat(s.n_lat_dof);
+  check(cudaStreamSynchronize(h->stream), "sync");
+  if (u) {
+    check(cudaMemcpy(lat.data(), h->U[h->cur], lat.size() * sizeof(double), cudaMemcpyDeviceToHost), "u");
+    h->from_lattice(lat, u);
+  }
+  if (u_prev) {
+    check(cudaMemcpy(lat.data(), h->U[1 - h->cur], lat.size() * sizeof(double), cudaMemcpyDeviceToHost), "u_prev");
+    h->from_lattice(lat, u_prev);
+  }
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_set_state(ibfem_t* h, const double* u, const double* u_prev, int64_t step) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (!u || !u_prev || step < 0) return fail(IBFEM_ERR_ARG, "u, u_prev and step >= 0 required");
+  if (!h->have_dt) return fail(IBFEM_ERR_STATE, "set_dt before set_state");
+  IBFEM_TRY
+  std::vector<double> a, b;
+  h->to_lattice(u, a);
+  h->to_lattice(u_prev, b);
+  h->cur = 0;
+  check(cudaMemcpyAsync(h->U[0], a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "u");
+  check(cudaMemcpyAsync(h->U[1], b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "u_prev");
+  unsigned long long cnt[4] = {(unsigned long long)step, 0, 0, 0};
+  check(cudaMemcpyAsync(h->counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, h->stream), "counters");
+  check(cudaStreamSynchronize(h->stream), "set_state");
+  h->step = step;
+  h->ring_start = step;
+  h->have_init = true;
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (!x || !y) return fail(IBFEM_ERR_ARG, "null vector");
+  IBFEM_TRY
+  std::vector<double> lx;
+  h->to_lattice(x, lx);
+  check(cudaMemcpyAsync(h->W, lx.data(), lx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "x");
+  OpInput in{h->W, nullptr, nullptr};
+  check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
+  check(launch_op_fp64(h->dev, in, h->scratch, kModeApply, nullptr, h->stream), "apply");
+  check(cudaMemcpyAsync(lx.data(), h->scratch, lx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "y");
+  check(cudaStreamSynchronize(h->stream), "apply sync");
+  h->from_lattice(lx, y);
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_crit_dt(ibfem_t* h, int max_iter, double rtol, double* dt_crit, double* lambda_max,
+                  int* iterations) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (max_iter < 1) return fail(IBFEM_ERR_ARG, "max_iter must be >= 1");
+  IBFEM_TRY
+  const Setup& s = h->setup;
+  // start vector v_i = 1 + 0.5 sin(i) over kept DOFs, normalised
+  std::vector<double> v(s.n_dof);
+  double nrm = 0;
+  for (int64_t i = 0; i < s.n_dof; ++i) {
+    v[i] = 1.0 + 0.5 * std::sin((double)i);
+    nrm += v[i] * v[i];
+  }
+  nrm = std::sqrt(nrm);
+  for (auto& x : v) x /= nrm;
+  std::vector<double> lv;
+  h->to_lattice(v.data(), lv);
+  double* bufs[2] = {h->W, h->scratch};
+  check(cudaMemcpyAsync(bufs[0], lv.data(), lv.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "start");
+  double one = 1.0;
+  double* inv_norm = h->scalars;
+  check(cudaMemcpyAsync(inv_norm, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream), "scal");
+  std::vector<double> hist;
+  double lam = 0, lam_old = 0;
+  int it = 0, b = 0;
+  bool have_old = false, converged = false;
+  while (it < max_iter && !converged) {
+    int chunk = std::min(kPowerChunk, max_iter - it);
+    for (int c = 0; c < chunk; ++c) {
+      OpInput x{bufs[b], h->dev.sinv, inv_norm};
+      check(launch_cut_apply_fp64(h->dev, x, false, h->stream), "cut_apply");
+      check(launch_op_fp64(h->dev, x, bufs[1 - b], kModePower, h->partials, h->stream), "power");
+      check(launch_reduce_power(h->partials, h->n_blocks, h->lam_hist, inv_norm, c, h->stream), "reduce");
+      b ^= 1;
+    }
+    hist.resize(chunk);
+    check(cudaMemcpyAsync(hist.data(), h->lam_hist, chunk * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "hist");
+    check(cudaStreamSynchronize(h->stream), "power sync");
+    for (int c = 0; c < chunk; ++c) {
+      ++it;
+      lam = hist[c];
+      if (have_old && std::fabs(lam - lam_old) <= rtol * std::fabs(lam)) {
+        converged = true;
+        break;
+      }
+      lam_old = lam;
+      have_old = true;
+    }
+  }
+  if (!(lam > 0) || !std::isfinite(lam)) throw std::runtime_error("power iteration produced a non-positive eigenvalue");
+  if (lambda_max) *lambda_max = lam;
+  if (dt_crit) *dt_crit = 2.0 / std::sqrt(lam);
+  if (iterations) *iterations = it;
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_get_lumped_mass(ibfem_t* h, double* ml) {
+  if (!h || !ml) return fail(IBFEM_ERR_ARG, "null argument");
+  h->from_lattice(h->setup.ML, ml);
+  return IBFEM_OK;
+}
+
+int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells) {
+  if (!h || !cells) return fail(IBFEM_ERR_ARG, "null argument");
+  std::copy(h->setup.cut_cells.begin(), h->setup.cut_cells.end(), cells);
+  return IBFEM_OK;
+}
+
+int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml) {
+  if (!h) return fail(IBFEM_ERR_ARG, "null handle");
+  const Setup& s = h->setup;
+  if (cell < 0 || cell >= s.n_elem || s.cls[cell] == kOutside) return fail(IBFEM_ERR_ARG, "cell is outside or out of range");
+  const int nl = s.n_loc;
+  if (s.cls[cell] == kCut) {
+    int ci = s.cut_index[cell];
+    if (K) std::copy(&s.Kcut[(size_t)ci * nl * nl], &s.Kcut[(size_t)(ci + 1) * nl * nl], K);
+    if (ml) std::copy(&s.mlcut[(size_t)ci * nl], &s.mlcut[(size_t)(ci + 1) * nl], ml);
+  } else {
+    if (K) std::copy(s.Kref.begin(), s.Kref.end(), K);
+    if (ml) std::copy(s.mref.begin(), s.mref.end(), ml);
+  }
+  return IBFEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// The opaque handle behind ibfem_t (runtime side only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/ibfem.h"
+#include "host_setup.h"
+#include "internal.h"
+
+namespace ibfem {
+
+constexpr int kGraphSteps = 32;   // steps per captured graph (even: parity preserved)
+constexpr int kPowerChunk = 32;   // power iterations between host convergence checks
+
+struct Handle {
+  ibfem_options opt{};
+  SetupInput input;
+  Setup setup;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevProblem dev{};
+  int tile[3] = {1, 1, 1};
+  int n_blocks = 0;
+  double* U[2] = {nullptr, nullptr};  // U[cur] = u^k, U[1 - cur] = u^{k-1}
+  int cur = 0;
+  double* W = nullptr;                 // work vector (power iteration, apply)
+  double* scratch = nullptr;
+  double* d_minv = nullptr;
+  double* partials = nullptr;
+  double* scalars = nullptr;
+  double* lam_hist = nullptr;
+  double* obs_out = nullptr;
+  unsigned long long* counters = nullptr;
+  cudaGraphExec_t graphs[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  bool have_dt = false, have_init = false;
+  double dt = 0.0;
+  int64_t step = 0, ring_start = 0;
+
+  void* dalloc(size_t bytes);
+  void dfree_all();
+  template <typename T>
+  T* upload(const std::vector<T>& v);
+  void to_lattice(const double* kept, std::vector<double>& lat) const;
+  void from_lattice(const std::vector<double>& lat, double* kept) const;
+  void build_device();
+  void invalidate_graphs();
+  // optional per-kernel timing: when `timing` is set, enqueue_step records an event
+  // pair around every launch and accumulates into slot_ms after a synchronise
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_slot;
+  size_t ev_used = 0;
+  double slot_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int n_slots = 0;
+  const char* slot_name[8] = {"", "", "", "", "", "", "", ""};
+  void timed_begin(int slot);
+  void timed_end();
+  void timed_collect();
+  void enqueue_step(int cur);
+  void run_steps(int64_t n);
+};
+
+}  // namespace ibfem
+
+struct ibfem_s : ibfem::Handle {};

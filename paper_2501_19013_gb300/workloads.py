@@ -159,6 +159,26 @@ def default_observers(dim: int) -> np.ndarray:
                      [0.9, 0.5, 0.5]], dtype=np.float64)
 
 
+def observers_outside_holes(pts: np.ndarray, holes: Optional[np.ndarray]) -> np.ndarray:
+    """Move observer points that fall inside a hole radially to 1.05 r from its centre."""
+    pts = np.array(pts, dtype=np.float64)
+    if holes is None:
+        return pts
+    d = pts.shape[1]
+    for i in range(len(pts)):
+        for row in holes:
+            c, r = row[:d], row[d]
+            v = pts[i] - c
+            dist = float(np.sqrt(np.sum(v * v)))
+            if dist < r * 1.05:
+                if dist == 0.0:
+                    v = np.zeros(d)
+                    v[0] = 1.0
+                    dist = 1.0
+                pts[i] = c + v / dist * r * 1.05
+    return pts
+
+
 def plate_one_hole() -> Workload:
     return Workload(name="plate_one_hole_16x16_p2", dim=2, n=(16, 16), p=2,
                     physics="scalar", alpha=1e-5, quad_depth=3,
@@ -175,7 +195,7 @@ def plate_holes_elastic(n: int = 256, p: int = 4, count: int = 12, seed: int = 0
                     quad_depth=3, holes=holes, stab="evs", eps=1e-4, f_lambda=1e-2,
                     source={"kind": "edge_traction", "y0": 0.4, "y1": 0.6,
                             "t": [1.0, 0.0]},
-                    f0=10.0, steps=steps, observers=default_observers(2))
+                    f0=10.0, steps=steps, observers=observers_outside_holes(default_observers(2), holes))
 
 
 def plate_holes_imex(n: int = 512, p: int = 3, count: int = 12, seed: int = 0,
@@ -185,18 +205,19 @@ def plate_holes_imex(n: int = 512, p: int = 3, count: int = 12, seed: int = 0,
                     physics="scalar", alpha=1e-12, quad_depth=3, holes=holes,
                     stab="none" if scheme == "imex" else "mass_scaling",
                     scheme=scheme, source={"kind": "point", "x": [0.1, 0.5]},
-                    f0=10.0, steps=steps, observers=default_observers(2))
+                    f0=10.0, steps=steps, observers=observers_outside_holes(default_observers(2), holes))
 
 
 def porous_voxel(n: int = 64, vn: int = 128, p: int = 3, seed: int = 0,
                  steps: int = 2000, porosity: float = 0.30) -> Workload:
     img = random_void_image(vn, 4.0 * vn / 128.0, 12.0 * vn / 128.0, porosity, seed)
     xs = nearest_solid_point(img, np.array([0.1, 0.5, 0.5]))
+    obs = np.array([nearest_solid_point(img, x) for x in default_observers(3)])
     return Workload(name=f"porous_voxel_{n}^3_p{p}", dim=3, n=(n, n, n), p=p,
                     physics="scalar", alpha=1e-5, quad_depth=1, voxels=img,
                     stab="evs", eps=1e-4, f_lambda=1e-2,
                     source={"kind": "point", "x": list(xs)}, f0=10.0, steps=steps,
-                    observers=default_observers(3))
+                    observers=obs)
 
 
 WORKLOADS = {

@@ -1,0 +1,58 @@
+"""Shared helpers of the parity tests: run a workload through the oracle and the library."""
+import numpy as np
+
+from oracle import discretization as OD, eigen, integrators as OI
+from paper_2501_19013_gb300 import workloads as W
+
+
+def oracle_disc(w, **kw):
+    return OD.from_workload(w, **kw)
+
+
+def oracle_dt(disc, factor=0.9):
+    return factor * eigen.dt_crit(eigen.dense_lambda_max(disc.K, disc.ML))
+
+
+def oracle_cdm(w, disc, dt, steps, u0=None, v0=None):
+    F = OD.source_vector(disc, w.source) if w.source else None
+    obs = disc.observer_matrix(w.observers) if w.observers is not None else None
+    u, up, samples = OI.cdm(disc.K, disc.ML, dt, steps, u0=u0, v0=v0, F=F, f_e=w.f0, obs=obs)
+    return u, up, samples
+
+
+def gpu_solver(w, precision="fp64", **kw):
+    from paper_2501_19013_gb300 import ibfem as ib
+    s = ib.from_workload(w, precision=precision, **kw)
+    if w.source:
+        kind, params = ib.source_params(w)
+        s.set_source(kind, params, w.f0)
+    if w.observers is not None:
+        s.set_observers(w.observers, capacity=max(w.steps, 1))
+    return s
+
+
+def gpu_cdm(w, dt, steps, u0=None, v0=None, precision="fp64"):
+    s = gpu_solver(w, precision)
+    s.set_dt(dt)
+    s.set_initial(u0, v0)
+    s.step(steps)
+    s.sync()
+    u, up = s.get_state()
+    samples = s.sample(steps + 1) if w.observers is not None else None
+    s.close()
+    return u, up, samples
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+SMALL_CASES = {
+    "plate_one_hole": lambda: W.plate_one_hole(),
+    "elastic_evs": lambda: W.plate_holes_elastic(n=24, p=4, count=3, steps=200),
+    "elastic_evs_ragged": lambda: W.plate_holes_elastic(n=19, p=2, count=2, seed=3, steps=150),
+    "scalar_mass_scaling": lambda: W.plate_holes_imex(n=30, p=3, count=3, scheme="cdm", steps=200),
+    "voxel_3d_evs": lambda: W.porous_voxel(n=6, vn=12, p=3, steps=100),
+    "voxel_3d_p2_ragged": lambda: W.porous_voxel(n=7, vn=14, p=2, seed=2, steps=100),
+}

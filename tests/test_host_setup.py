@@ -1,0 +1,63 @@
+"""Host-side discretisation of the library against the oracle (no GPU needed: the
+library is created with host_only=1, which runs the C++ setup and no device code)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import discretization as OD
+from oracle.geometry import Holes, Voxels
+from paper_2501_19013_gb300 import workloads as W
+
+ib = pytest.importorskip("paper_2501_19013_gb300.ibfem")
+if not os.path.exists(ib.LIB_PATH):
+    pytest.skip("libibfem.so not built", allow_module_level=True)
+
+
+def compare(w, rtol=1e-11):
+    d = OD.from_workload(w)
+    s = ib.from_workload(w, host_only=True)
+    inf = s.info()
+    assert inf.n_dof == d.n_dof
+    assert inf.n_cut == len(d.cut) and inf.n_uncut == len(d.uncut)
+    np.testing.assert_array_equal(s.cut_cells(), d.cut)
+    ml = s.lumped_mass()
+    np.testing.assert_allclose(ml, d.ML, rtol=rtol, atol=0)
+    Kr, mr = s.element(d.uncut[0])
+    np.testing.assert_allclose(Kr, d.K_ref, rtol=rtol, atol=rtol * np.abs(d.K_ref).max())
+    np.testing.assert_allclose(mr, d.m_gll, rtol=rtol)
+    for e in d.cut[:: max(1, len(d.cut) // 25)]:
+        K, m = s.element(e)
+        np.testing.assert_allclose(K, d.K_cut[e], rtol=rtol, atol=rtol * np.abs(d.K_cut[e]).max())
+        np.testing.assert_allclose(m, d.ml_cut[e], rtol=1e-9, atol=1e-9 * m.max())
+    assert inf.lambda_ref == pytest.approx(d.lam_ref, rel=1e-11)
+    s.close()
+
+
+def test_plate_one_hole_setup():
+    compare(W.plate_one_hole())
+
+
+def test_elastic_evs_setup():
+    compare(W.plate_holes_elastic(n=24, p=4, count=3, steps=10))
+
+
+def test_mass_scaling_setup():
+    compare(W.plate_holes_imex(n=20, p=3, count=2, scheme="cdm"))
+
+
+def test_voxel_3d_evs_setup():
+    compare(W.porous_voxel(n=6, vn=12, p=2, steps=10))
+
+
+@pytest.mark.parametrize("p,ne,dofs", [(4, 9, 21109), (5, 7, 22706)])
+def test_rotated_cube_dofs_table3(p, ne, dofs):
+    """Library classifier + numbering reproduce the Table 3 DOF counts (Sec. 3.1)."""
+    from oracle.geometry import cardan_matrix
+    a = math.radians(10.0)
+    T = cardan_matrix(a, a, a, "zyx")
+    rb = np.concatenate([[0.3, 0.25, 0.25, 0.25], T.ravel()])
+    s = ib.Solver(3, (ne, ne, ne), p, lo=(0, 0, 0), hi=(0.5, 0.5, 0.5), rotated_box=rb,
+                  quad_depth=0, host_only=True)
+    assert s.info().n_dof == dofs
