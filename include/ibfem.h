@@ -181,10 +181,14 @@ int ibfem_set_dt(ibfem_t* h, double dt);
 int ibfem_step(ibfem_t* h, int64_t n);
 
 /* Same as ibfem_step, but every kernel is launched directly with a pair of CUDA events
- * around it on the handle's stream (no graph).  ms[slot] accumulates the device time of
- * kernel slot `slot` (at most max_slots slots, names from ibfem_kernel_name); *n_slots
- * receives the slot count.  Synchronises.  Meant for benchmarks and profiles.           */
-int ibfem_step_timed(ibfem_t* h, int64_t n, double* ms, int max_slots, int* n_slots);
+ * around it on the handle's stream (no graph).  When flush_bytes > 0, flush_buf (device
+ * memory of at least flush_bytes) is overwritten with cudaMemsetAsync before every step,
+ * outside the timed events, to evict the L2 cache.  ms[0] accumulates the device time of
+ * whole steps (first kernel start to last kernel end), ms[1 + k] that of kernel k (at most
+ * max_slots values; names from ibfem_kernel_name); *n_slots receives the slot count.
+ * Synchronises.  Meant for benchmarks and profiles.                                    */
+int ibfem_step_timed(ibfem_t* h, int64_t n, void* flush_buf, size_t flush_bytes, double* ms,
+                     int max_slots, int* n_slots);
 /* Name of kernel slot `slot` of ibfem_step_timed ("" if out of range). */
 const char* ibfem_kernel_name(const ibfem_t* h, int slot);
 

@@ -171,6 +171,13 @@ void Handle::timed_collect() {
     check(cudaEventElapsedTime(&ms, ev_pool[2 * i], ev_pool[2 * i + 1]), "elapsed");
     slot_ms[ev_slot[i]] += ms;
   }
+  for (size_t s = 0; s < step_first_ev.size(); ++s) {
+    float ms = 0.f;
+    check(cudaEventElapsedTime(&ms, ev_pool[step_first_ev[s]], ev_pool[step_last_ev[s]]), "elapsed");
+    slot_ms[0] += ms;
+  }
+  step_first_ev.clear();
+  step_last_ev.clear();
   ev_slot.clear();
   ev_used = 0;
 }
@@ -178,14 +185,16 @@ void Handle::timed_collect() {
 // One CDM step with u = U[cur], out = U[1 - cur] (in place over u^{k-1}).
 void Handle::enqueue_step(int cur) {
   OpInput x{U[cur], nullptr, nullptr};
-  slot_name[0] = "cut_apply_fp64";
-  slot_name[1] = "op_fp64_fused_cdm";
-  timed_begin(0);
+  slot_name[1] = "cut_apply_fp64";
+  slot_name[2] = "op_fp64_fused_cdm";
+  if (timing) step_first_ev.push_back(ev_used);
+  timed_begin(1);
   check(launch_cut_apply_fp64(dev, x, true, stream), "cut_apply");
   timed_end();
-  timed_begin(1);
+  timed_begin(2);
   check(launch_op_fp64(dev, x, U[1 - cur], kModeCDM, nullptr, stream), "op_fused");
   timed_end();
+  if (timing) step_last_ev.push_back(ev_used - 1);
 }
 
 void Handle::run_steps(int64_t n) {
@@ -534,15 +543,18 @@ int ibfem_step(ibfem_t* h, int64_t n) {
   IBFEM_CATCH
 }
 
-int ibfem_step_timed(ibfem_t* h, int64_t n, double* ms, int max_slots, int* n_slots) {
+int ibfem_step_timed(ibfem_t* h, int64_t n, void* flush_buf, size_t flush_bytes, double* ms,
+                     int max_slots, int* n_slots) {
   int rc = require_device(h);
   if (rc) return rc;
-  if (n < 0 || (max_slots > 0 && !ms)) return fail(IBFEM_ERR_ARG, "bad arguments");
+  if (n < 0 || (max_slots > 0 && !ms) || (flush_bytes > 0 && !flush_buf))
+    return fail(IBFEM_ERR_ARG, "bad arguments");
   if (!h->have_init) return fail(IBFEM_ERR_STATE, "set_initial (or set_state) before step");
   IBFEM_TRY
   for (double& v : h->slot_ms) v = 0.0;
   h->timing = true;
   for (int64_t i = 0; i < n; ++i) {
+    if (flush_bytes > 0) check(cudaMemsetAsync(flush_buf, (int)(i & 0xff), flush_bytes, h->stream), "flush");
     h->enqueue_step(h->cur);
     h->cur ^= 1;
     if (h->ev_used > 512) h->timed_collect();

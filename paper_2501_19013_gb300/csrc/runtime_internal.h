@@ -54,9 +54,10 @@ struct Handle {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_slot;
   size_t ev_used = 0;
+  std::vector<size_t> step_first_ev, step_last_ev;
   double slot_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int n_slots = 0;
-  const char* slot_name[8] = {"", "", "", "", "", "", "", ""};
+  int n_slots = 1;
+  const char* slot_name[8] = {"step", "", "", "", "", "", "", ""};
   void timed_begin(int slot);
   void timed_end();
   void timed_collect();

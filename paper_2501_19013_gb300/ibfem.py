@@ -91,7 +91,7 @@ def lib():
         "ibfem_set_dt": (C.c_int, [vp, C.c_double]),
         "ibfem_step": (C.c_int, [vp, C.c_int64]),
         "ibfem_sync": (C.c_int, [vp]),
-        "ibfem_step_timed": (C.c_int, [vp, C.c_int64, DP, C.c_int, C.POINTER(C.c_int)]),
+        "ibfem_step_timed": (C.c_int, [vp, C.c_int64, vp, C.c_size_t, DP, C.c_int, C.POINTER(C.c_int)]),
         "ibfem_kernel_name": (C.c_char_p, [vp, C.c_int]),
         "ibfem_sample": (C.c_int, [vp, C.c_int64, DP, C.POINTER(C.c_int64)]),
         "ibfem_get_state": (C.c_int, [vp, DP, DP]),
@@ -240,11 +240,14 @@ class Solver:
     def step(self, n):
         _check(lib().ibfem_step(self.h, int(n)))
 
-    def step_timed(self, n):
-        """Run n steps with per-kernel CUDA events; returns {kernel name: total ms}."""
+    def step_timed(self, n, flush_ptr=None, flush_bytes=0):
+        """Run n steps with per-kernel CUDA events (optionally writing ``flush_bytes`` at
+        device address ``flush_ptr`` before each step); returns {slot name: total ms},
+        slot "step" being whole steps."""
         ms = np.zeros(8)
         ns = C.c_int()
-        _check(lib().ibfem_step_timed(self.h, int(n), _dp(ms), 8, C.byref(ns)))
+        _check(lib().ibfem_step_timed(self.h, int(n), flush_ptr, int(flush_bytes), _dp(ms), 8,
+                                      C.byref(ns)))
         return {lib().ibfem_kernel_name(self.h, i).decode(): ms[i] for i in range(ns.value)}
 
     def sync(self):
