@@ -98,9 +98,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+GRID = 256
+
+
 def workload_for_bench():
     from paper_2501_19013_gb300 import workloads as W
-    return W.plate_holes_elastic()
+    return W.plate_holes_elastic(n=GRID)
 
 
 def window_workload():
@@ -172,8 +175,11 @@ def run_ours(args, rank, world, local_rank):
         s = build_solver(w, prec, sptr)
         info = s.info()
         if dt is None:
-            dt_crit, lam, it = s.crit_dt(max_iter=2000, rtol=1e-7)
-            dt = w.dt_factor * dt_crit
+            if args.dt > 0:
+                dt = args.dt
+            else:
+                dt_crit, lam, it = s.crit_dt(max_iter=2000, rtol=1e-7)
+                dt = w.dt_factor * dt_crit
         s.set_dt(dt)
         s.set_initial()
         s.step_timed(args.warmup, flush.data_ptr(), FLUSH_BYTES)
@@ -197,9 +203,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         steady_ms = e0.elapsed_time(e1) / args.steps
         # accuracy over the configured run (from rest, with the load)
+        run_steps = w.steps if args.run_steps < 0 else args.run_steps
         s.set_initial()
         t0 = time.perf_counter()
-        s.step(w.steps)
+        s.step(run_steps)
         s.sync()
         run_s = time.perf_counter() - t0
         u_end, _ = s.get_state()
@@ -272,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
         variants_out[p] = {"dof_steps_per_s": r["info"].n_dof / (r["step_ms"] * 1e-3),
                            "ms_per_step": r["step_ms"], "steady_state_ms_per_step": r["steady_ms"],
                            "rel_l2_vs_fp64_after_run": r["rel_l2"],
-                           "run_steps": w.steps,
+                           "run_steps": w.steps if args.run_steps < 0 else args.run_steps,
                            "time_to_accuracy_s": (r["step_ms"] * 1e-3 * w.steps) if (r["rel_l2"] is not None and r["rel_l2"] <= 1e-4) else None,
                            "kernels_ms": r["kernels"]}
     launches = args.steps * len(rb["kernels"])
@@ -302,7 +309,12 @@ def main():
     ap.add_argument("--precisions", default="fp64")
     ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=256, help="cells per axis of the plate (profiling)")
+    ap.add_argument("--dt", type=float, default=0.0, help="fixed dt instead of 0.9 dt_crit (profiling)")
+    ap.add_argument("--run-steps", type=int, default=-1, help="steps of the accuracy run (-1: the workload's)")
     args = ap.parse_args()
+    global GRID
+    GRID = args.grid
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
