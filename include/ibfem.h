@@ -218,6 +218,40 @@ int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells);
  * matrix for uncut cells); optional lumped diagonal (n_loc). Errors: ARG (outside).   */
 int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml);
 
+/* ---- allocation-free operator ----------------------------------------------------- */
+
+/* y = K x on the node lattice, for callers that cannot allocate device memory: an
+ * application whose own fixed pool or arena owns the GPU memory, or a latency-critical
+ * loop where cudaMalloc/cudaFree (which may synchronise the device) are off-limits.  This
+ * is an addition of this library; the paper has no counterpart.
+ *
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).  Its
+ * only scratch, the products K^e x_e of the cut cells, lives in a static device array of
+ * 2^19 doubles (4 MiB) that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current); make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents; every entry a call reads is
+ * written by the same call first, so nothing needs clearing.  Calls whose kernels overlap
+ * on the GPU (different streams, or different threads) race on the array: serialise them.
+ *
+ * Arguments (all pointers are device memory owned by the caller, read-only except y):
+ *   dim, p, ncomp   2 or 3; GLL order; 1 (scalar) or 2 (plane strain, dim 2)
+ *   n_cells[dim]    cells per axis; the lattice has n_cells[k] p + 1 nodes per axis
+ *   cell_class      one byte per cell, x fastest: 0 outside, 1 cut, 2 uncut
+ *   cut_index       int32 per cell: index into the cut list, -1 if not cut
+ *   cut_cells       n_cut int64: cell of each cut index
+ *   K_ref           n_loc x n_loc reference stiffness of an uncut cell (n_loc = (p+1)^dim ncomp)
+ *   K_cut           n_cut x n_loc x n_loc stiffness of the cut cells (symmetric, row-major)
+ *   x, y            lattice vectors, node-major with ncomp interleaved; y is overwritten
+ *   stream          cudaStream_t (NULL = legacy stream); the call only enqueues work
+ * Errors: IBFEM_ERR_ARG for a null pointer, an unsupported (dim, p, ncomp) or
+ * n_cut * n_loc above 2^19 (message names the sizes); IBFEM_ERR_CUDA for a launch error. */
+int ibfem_apply_operator_noalloc(int dim, int p, int ncomp, const int n_cells[3],
+                                 const uint8_t* cell_class, const int32_t* cut_index,
+                                 const int64_t* cut_cells, int64_t n_cut,
+                                 const double* K_ref, const double* K_cut,
+                                 const double* x, double* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -242,6 +242,11 @@ void Handle::run_steps(int64_t n) {
   catch (const std::domain_error& e) { return fail(IBFEM_ERR_GEOMETRY, e.what()); } \
   catch (const std::exception& e) { return fail(IBFEM_ERR_EIG, e.what()); }
 
+namespace ibfem {
+// lets other translation units report through ibfem_last_error()
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ibfem
+
 extern "C" {
 
 const char* ibfem_last_error(void) { return g_last_error.c_str(); }

@@ -100,6 +100,8 @@ def lib():
         "ibfem_get_lumped_mass": (C.c_int, [vp, DP]),
         "ibfem_get_cut_cells": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "ibfem_get_element": (C.c_int, [vp, C.c_int64, DP, DP]),
+        "ibfem_apply_operator_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                                   vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -292,6 +294,15 @@ class Solver:
         ml = np.zeros(self.n_loc)
         _check(lib().ibfem_get_element(self.h, int(cell), _dp(K), _dp(ml)))
         return K, ml
+
+
+def apply_operator_noalloc(dim, p, ncomp, n_cells, cell_class, cut_index, cut_cells, n_cut,
+                           K_ref, K_cut, x, y, stream=None):
+    """Forward to ``ibfem_apply_operator_noalloc``; every array argument is a device address
+    (int), ``stream`` a cudaStream_t handle (int) or None."""
+    nc = (C.c_int * 3)(*[int(v) for v in list(n_cells) + [1] * (3 - len(n_cells))])
+    _check(lib().ibfem_apply_operator_noalloc(dim, p, ncomp, nc, cell_class, cut_index, cut_cells,
+                                              int(n_cut), K_ref, K_cut, x, y, stream))
 
 
 def from_workload(w, precision="fp64", host_only=False, scheme=None, **kw):
