@@ -13,6 +13,8 @@
 #include "host_setup.h"
 
 #include <algorithm>
+#include <array>
+#include <climits>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -784,6 +786,383 @@ Setup build_setup(const SetupInput& in) {
     }
   }
   return s;
+}
+
+}  // namespace ibfem
+
+// ====================================================================== IMEX (host)
+namespace ibfem {
+
+namespace {
+
+// Geometric nested dissection of one connected vertex set: split along the longest axis
+// at the median, take the vertices of the upper half adjacent to the lower half as the
+// separator, order lower half, upper half, separator (recursively).
+void nested_dissection(std::vector<int64_t>& verts, const std::vector<int64_t>& Ap,
+                       const std::vector<int64_t>& Ai, const std::vector<std::array<int64_t, 3>>& xyz,
+                       std::vector<int32_t>& tag, int32_t& next_tag, std::vector<int64_t>& out) {
+  const size_t kLeaf = 24;
+  if (verts.size() <= kLeaf) {
+    out.insert(out.end(), verts.begin(), verts.end());
+    return;
+  }
+  int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
+  for (int64_t v : verts)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], xyz[v][k]);
+      hi[k] = std::max(hi[k], xyz[v][k]);
+    }
+  int axis = 0;
+  for (int k = 1; k < 3; ++k)
+    if (hi[k] - lo[k] > hi[axis] - lo[axis]) axis = k;
+  if (hi[axis] == lo[axis]) {
+    out.insert(out.end(), verts.begin(), verts.end());
+    return;
+  }
+  std::sort(verts.begin(), verts.end(), [&](int64_t a, int64_t b) {
+    return xyz[a][axis] != xyz[b][axis] ? xyz[a][axis] < xyz[b][axis] : a < b;
+  });
+  int64_t split = xyz[verts[verts.size() / 2]][axis];
+  if (split == xyz[verts[0]][axis]) split += 1;  // keep both halves non-empty
+  int32_t tA = next_tag++;
+  std::vector<int64_t> A, B, S;
+  for (int64_t v : verts)
+    if (xyz[v][axis] < split) {
+      A.push_back(v);
+      tag[v] = tA;
+    }
+  for (int64_t v : verts) {
+    if (xyz[v][axis] < split) continue;
+    bool sep = false;
+    for (int64_t p = Ap[v]; p < Ap[v + 1] && !sep; ++p)
+      if (tag[Ai[p]] == tA) sep = true;
+    (sep ? S : B).push_back(v);
+  }
+  if (A.empty() || (B.empty() && S.size() == verts.size())) {
+    out.insert(out.end(), verts.begin(), verts.end());
+    return;
+  }
+  nested_dissection(A, Ap, Ai, xyz, tag, next_tag, out);
+  nested_dissection(B, Ap, Ai, xyz, tag, next_tag, out);
+  out.insert(out.end(), S.begin(), S.end());
+}
+
+// Elimination tree of a symmetric matrix given by its full CSR pattern.
+void etree(int64_t n, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
+           std::vector<int64_t>& parent) {
+  std::vector<int64_t> anc(n, -1);
+  parent.assign(n, -1);
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t p = Ap[k]; p < Ap[k + 1]; ++p) {
+      int64_t j = Ai[p];
+      while (j != -1 && j < k) {
+        int64_t nx = anc[j];
+        anc[j] = k;
+        if (nx == -1) parent[j] = k;
+        j = nx;
+      }
+    }
+}
+
+// Nonzero pattern of row k of L (columns < k) in topological order: s[top..n).
+int64_t row_pattern(int64_t k, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
+                    const std::vector<int64_t>& parent, std::vector<int64_t>& s,
+                    std::vector<int64_t>& mark, std::vector<int64_t>& path) {
+  int64_t n = (int64_t)s.size(), top = n;
+  mark[k] = k;
+  for (int64_t p = Ap[k]; p < Ap[k + 1]; ++p) {
+    int64_t j = Ai[p];
+    if (j >= k) continue;
+    int64_t len = 0;
+    while (mark[j] != k) {
+      path[len++] = j;
+      mark[j] = k;
+      j = parent[j];
+    }
+    while (len > 0) s[--top] = path[--len];
+  }
+  return top;
+}
+
+}  // namespace
+
+bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
+                     const std::vector<double>& Ax, SparseChol& out, std::string& err) {
+  // Up-looking factorisation A = L L^T, one row of L at a time; L kept by columns (CSC),
+  // diagonal first in each column, which is the CSR of L^T used by the backward solve.
+  std::vector<int64_t> parent, s(n), mark(n, -1), path(n);
+  etree(n, Ap, Ai, parent);
+  std::vector<int64_t> cnt(n, 1);
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t top = row_pattern(k, Ap, Ai, parent, s, mark, path);
+    for (int64_t t = top; t < n; ++t) cnt[s[t]]++;
+  }
+  std::vector<int64_t> Cp(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j) Cp[j + 1] = Cp[j] + cnt[j];
+  std::vector<int64_t> Ci(Cp[n]);
+  std::vector<double> Cx(Cp[n]);
+  std::vector<int64_t> fill(n);
+  for (int64_t j = 0; j < n; ++j) fill[j] = Cp[j] + 1;
+  std::vector<double> x(n, 0.0);
+  std::fill(mark.begin(), mark.end(), -1);
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t top = row_pattern(k, Ap, Ai, parent, s, mark, path);
+    double d = 0.0;
+    for (int64_t p = Ap[k]; p < Ap[k + 1]; ++p) {
+      int64_t j = Ai[p];
+      if (j < k) x[j] = Ax[p];
+      else if (j == k) d = Ax[p];
+    }
+    for (int64_t t = top; t < n; ++t) {
+      int64_t i = s[t];
+      double lki = x[i] / Cx[Cp[i]];
+      x[i] = 0.0;
+      for (int64_t p = Cp[i] + 1; p < fill[i]; ++p) x[Ci[p]] -= Cx[p] * lki;
+      d -= lki * lki;
+      Ci[fill[i]] = k;
+      Cx[fill[i]] = lki;
+      fill[i]++;
+    }
+    if (!(d > 0.0)) {
+      err = "matrix is not positive definite at row " + std::to_string(k);
+      return false;
+    }
+    Ci[Cp[k]] = k;
+    Cx[Cp[k]] = std::sqrt(d);
+  }
+  out.n = n;
+  out.Up = Cp;
+  out.Ui = Ci;
+  out.Ux = Cx;
+  // CSR of L (rows), diagonal last
+  std::vector<int64_t> rc(n, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = Cp[j]; p < Cp[j + 1]; ++p) rc[Ci[p]]++;
+  out.Lp.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) out.Lp[i + 1] = out.Lp[i] + rc[i];
+  out.Li.assign(out.Lp[n], 0);
+  out.Lx.assign(out.Lp[n], 0.0);
+  std::vector<int64_t> pos(out.Lp.begin(), out.Lp.end() - 1);
+  for (int64_t j = 0; j < n; ++j)   // columns in increasing order -> diagonal lands last
+    for (int64_t p = Cp[j]; p < Cp[j + 1]; ++p) {
+      int64_t i = Ci[p];
+      out.Li[pos[i]] = j;
+      out.Lx[pos[i]] = Cx[p];
+      pos[i]++;
+    }
+  return true;
+}
+
+void imex_partition(const Setup& s, ImexData& d) {
+  const int nl = s.n_loc, nc = s.ncomp;
+  d.c_of_dof.assign(s.n_lat_dof, -1);
+  std::vector<uint8_t> isc(s.n_lat_dof, 0);
+  for (int64_t ci = 0; ci < s.n_cut; ++ci) {
+    int64_t cell = s.cut_cells[ci];
+    for (int l = 0; l < s.nn_loc; ++l) {
+      int64_t node = lattice_node(s, cell, l);
+      for (int c = 0; c < nc; ++c) isc[node * nc + c] = 1;
+    }
+  }
+  d.c_dof.clear();
+  for (int64_t g = 0; g < s.n_lat_dof; ++g)
+    if (isc[g]) {
+      d.c_of_dof[g] = (int64_t)d.c_dof.size();
+      d.c_dof.push_back(g);
+    }
+  d.n_c = (int64_t)d.c_dof.size();
+  // cells touching the c-set
+  d.ccells.clear();
+  std::vector<int64_t> loc_dof(nl);
+  for (int64_t e = 0; e < s.n_elem; ++e) {
+    if (s.cls[e] == kOutside) continue;
+    bool any = false;
+    for (int l = 0; l < s.nn_loc && !any; ++l)
+      if (isc[lattice_node(s, e, l) * nc]) any = true;
+    if (any) d.ccells.push_back(e);
+  }
+  // pattern of S over c indices: union of c-c couplings of the c-cells
+  std::vector<std::vector<int64_t>> rows(d.n_c);
+  for (int64_t e : d.ccells) {
+    for (int l = 0; l < s.nn_loc; ++l)
+      for (int c = 0; c < nc; ++c) loc_dof[l * nc + c] = d.c_of_dof[lattice_node(s, e, l) * nc + c];
+    bool cut = s.cls[e] == kCut;
+    for (int a = 0; a < nl; ++a) {
+      if (loc_dof[a] < 0) continue;
+      for (int b = 0; b < nl; ++b) {
+        if (loc_dof[b] < 0) continue;
+        if (!cut && s.Kref[(size_t)a * nl + b] == 0.0 && a != b) continue;
+        rows[loc_dof[a]].push_back(loc_dof[b]);
+      }
+    }
+  }
+  d.Sp.assign(d.n_c + 1, 0);
+  for (int64_t i = 0; i < d.n_c; ++i) {
+    auto& r = rows[i];
+    r.push_back(i);
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    d.Sp[i + 1] = d.Sp[i] + (int64_t)r.size();
+  }
+  d.Si.resize(d.Sp[d.n_c]);
+  for (int64_t i = 0; i < d.n_c; ++i) std::copy(rows[i].begin(), rows[i].end(), d.Si.begin() + d.Sp[i]);
+  rows.clear();
+  // values of M^cc (consistent cut mass + nodal GLL mass of uncut cells) and K^cc
+  d.Mx.assign(d.Si.size(), 0.0);
+  d.Kx.assign(d.Si.size(), 0.0);
+  auto slot = [&](int64_t i, int64_t j) {
+    auto b = d.Si.begin() + d.Sp[i], en = d.Si.begin() + d.Sp[i + 1];
+    return (int64_t)(std::lower_bound(b, en, j) - d.Si.begin());
+  };
+  for (int64_t e : d.ccells) {
+    for (int l = 0; l < s.nn_loc; ++l)
+      for (int c = 0; c < nc; ++c) loc_dof[l * nc + c] = d.c_of_dof[lattice_node(s, e, l) * nc + c];
+    bool cut = s.cls[e] == kCut;
+    const double* K = cut ? &s.Kcut[(size_t)s.cut_index[e] * nl * nl] : s.Kref.data();
+    const double* M = cut ? &s.Mcut[(size_t)s.cut_index[e] * nl * nl] : nullptr;
+    for (int a = 0; a < nl; ++a) {
+      if (loc_dof[a] < 0) continue;
+      for (int b = 0; b < nl; ++b) {
+        if (loc_dof[b] < 0) continue;
+        double kv = K[(size_t)a * nl + b];
+        double mv = cut ? M[(size_t)a * nl + b] : (a == b ? s.mref[a] : 0.0);
+        if (kv == 0.0 && mv == 0.0) continue;
+        int64_t p = slot(loc_dof[a], loc_dof[b]);
+        d.Kx[p] += kv;
+        d.Mx[p] += mv;
+      }
+    }
+  }
+  // ordering: connected components (BFS), nested dissection inside each
+  std::vector<std::array<int64_t, 3>> xyz(d.n_c);
+  for (int64_t i = 0; i < d.n_c; ++i) {
+    int64_t node = d.c_dof[i] / nc, rem = node;
+    for (int k = 0; k < 3; ++k) {
+      xyz[i][k] = k < s.dim ? rem % s.lat[k] : 0;
+      if (k < s.dim) rem /= s.lat[k];
+    }
+  }
+  std::vector<int32_t> comp(d.n_c, -1), tag(d.n_c, -1);
+  int32_t next_tag = 0;
+  d.perm.clear();
+  d.comp_ptr.assign(1, 0);
+  std::vector<int64_t> queue;
+  for (int64_t r = 0; r < d.n_c; ++r) {
+    if (comp[r] >= 0) continue;
+    int32_t cid = (int32_t)d.comp_ptr.size() - 1;
+    queue.assign(1, r);
+    comp[r] = cid;
+    for (size_t q = 0; q < queue.size(); ++q) {
+      int64_t v = queue[q];
+      for (int64_t p = d.Sp[v]; p < d.Sp[v + 1]; ++p)
+        if (comp[d.Si[p]] < 0) {
+          comp[d.Si[p]] = cid;
+          queue.push_back(d.Si[p]);
+        }
+    }
+    nested_dissection(queue, d.Sp, d.Si, xyz, tag, next_tag, d.perm);
+    d.comp_ptr.push_back((int32_t)d.perm.size());
+  }
+  d.iperm.assign(d.n_c, 0);
+  for (int64_t r = 0; r < d.n_c; ++r) d.iperm[d.perm[r]] = r;
+  // residual gather lists (permuted rows): entries slot * n_loc + loc over the c-cells
+  std::vector<std::vector<int32_t>> g(d.n_c);
+  for (size_t sl = 0; sl < d.ccells.size(); ++sl) {
+    int64_t e = d.ccells[sl];
+    for (int l = 0; l < s.nn_loc; ++l)
+      for (int c = 0; c < nc; ++c) {
+        int64_t ci = d.c_of_dof[lattice_node(s, e, l) * nc + c];
+        if (ci >= 0) g[d.iperm[ci]].push_back((int32_t)(sl * nl + l * nc + c));
+      }
+  }
+  d.g_ptr.assign(d.n_c + 1, 0);
+  for (int64_t r = 0; r < d.n_c; ++r) d.g_ptr[r + 1] = d.g_ptr[r] + (int64_t)g[r].size();
+  d.g_idx.clear();
+  for (auto& v : g) d.g_idx.insert(d.g_idx.end(), v.begin(), v.end());
+}
+
+static void permuted(const ImexData& d, const std::vector<double>& vals, std::vector<int64_t>& P,
+                     std::vector<int64_t>& I, std::vector<double>& X) {
+  P.assign(d.n_c + 1, 0);
+  for (int64_t r = 0; r < d.n_c; ++r) P[r + 1] = P[r] + (d.Sp[d.perm[r] + 1] - d.Sp[d.perm[r]]);
+  I.resize(P[d.n_c]);
+  X.resize(P[d.n_c]);
+  std::vector<std::pair<int64_t, double>> row;
+  for (int64_t r = 0; r < d.n_c; ++r) {
+    int64_t i = d.perm[r];
+    row.clear();
+    for (int64_t p = d.Sp[i]; p < d.Sp[i + 1]; ++p) row.push_back({d.iperm[d.Si[p]], vals[p]});
+    std::sort(row.begin(), row.end());
+    for (size_t q = 0; q < row.size(); ++q) {
+      I[P[r] + q] = row[q].first;
+      X[P[r] + q] = row[q].second;
+    }
+  }
+}
+
+bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err) {
+  (void)s;
+  std::vector<double> Sx(d.Mx.size());
+  for (size_t p = 0; p < Sx.size(); ++p) Sx[p] = d.Mx[p] + beta_dt2 * d.Kx[p];
+  std::vector<int64_t> P, I;
+  std::vector<double> X;
+  permuted(d, Sx, P, I, X);
+  if (!sparse_cholesky(d.n_c, P, I, X, d.chol, err)) return false;
+  d.beta_dt2 = beta_dt2;
+  // level schedules per component
+  const SparseChol& L = d.chol;
+  std::vector<int32_t> lf(d.n_c, 0), lb(d.n_c, 0);
+  for (int64_t r = 0; r < d.n_c; ++r)
+    for (int64_t p = L.Lp[r]; p + 1 < L.Lp[r + 1]; ++p) lf[r] = std::max(lf[r], lf[L.Li[p]] + 1);
+  for (int64_t r = d.n_c - 1; r >= 0; --r)
+    for (int64_t p = L.Up[r] + 1; p < L.Up[r + 1]; ++p) lb[r] = std::max(lb[r], lb[L.Ui[p]] + 1);
+  d.chol.fwd_level_ptr.assign(1, 0);
+  d.chol.bwd_level_ptr.assign(1, 0);
+  d.chol.fwd_rows.clear();
+  d.chol.bwd_rows.clear();
+  d.comp_flvl.assign(1, 0);
+  d.comp_blvl.assign(1, 0);
+  for (size_t c = 0; c + 1 < d.comp_ptr.size(); ++c) {
+    for (int pass = 0; pass < 2; ++pass) {
+      const std::vector<int32_t>& lv = pass == 0 ? lf : lb;
+      std::vector<int32_t>& rows = pass == 0 ? d.chol.fwd_rows : d.chol.bwd_rows;
+      std::vector<int32_t>& ptr = pass == 0 ? d.chol.fwd_level_ptr : d.chol.bwd_level_ptr;
+      int32_t nlev = 0;
+      for (int32_t r = d.comp_ptr[c]; r < d.comp_ptr[c + 1]; ++r) nlev = std::max(nlev, lv[r] + 1);
+      std::vector<std::vector<int32_t>> by(nlev);
+      for (int32_t r = d.comp_ptr[c]; r < d.comp_ptr[c + 1]; ++r) by[lv[r]].push_back(r);
+      for (auto& b : by) {
+        rows.insert(rows.end(), b.begin(), b.end());
+        ptr.push_back((int32_t)rows.size());
+      }
+      (pass == 0 ? d.comp_flvl : d.comp_blvl).push_back((int32_t)ptr.size() - 1);
+    }
+  }
+  return true;
+}
+
+bool imex_mass_solve(const ImexData& d, const std::vector<double>& b, std::vector<double>& a,
+                     std::string& err) {
+  std::vector<int64_t> P, I;
+  std::vector<double> X;
+  permuted(d, d.Mx, P, I, X);
+  SparseChol c;
+  if (!sparse_cholesky(d.n_c, P, I, X, c, err)) return false;
+  std::vector<double> y(d.n_c);
+  for (int64_t r = 0; r < d.n_c; ++r) y[r] = b[d.perm[r]];
+  for (int64_t r = 0; r < d.n_c; ++r) {
+    double acc = y[r];
+    for (int64_t p = c.Lp[r]; p + 1 < c.Lp[r + 1]; ++p) acc -= c.Lx[p] * y[c.Li[p]];
+    y[r] = acc / c.Lx[c.Lp[r + 1] - 1];
+  }
+  for (int64_t r = d.n_c - 1; r >= 0; --r) {
+    double acc = y[r];
+    for (int64_t p = c.Up[r] + 1; p < c.Up[r + 1]; ++p) acc -= c.Ux[p] * y[c.Ui[p]];
+    y[r] = acc / c.Ux[c.Up[r]];
+  }
+  a.assign(d.n_c, 0.0);
+  for (int64_t r = 0; r < d.n_c; ++r) a[d.perm[r]] = y[r];
+  return true;
 }
 
 }  // namespace ibfem

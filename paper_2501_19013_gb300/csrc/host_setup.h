@@ -105,8 +105,35 @@ struct SparseChol {
 bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
                      const std::vector<double>& Ax, SparseChol& out, std::string& err);
 
-// Reverse Cuthill-McKee ordering of a symmetric pattern; perm[new] = old.
-std::vector<int64_t> rcm_order(int64_t n, const std::vector<int64_t>& Ap,
-                               const std::vector<int64_t>& Ai);
+// IMEX partition (Sec. 2.6, Algorithm 2): the c-set (DOFs with support in a cut cell),
+// the consistent M^cc and K^cc on it, and the Cholesky factor of S = M^cc + beta dt^2 K^cc
+// in a fill-reducing order (connected components, then geometric nested dissection), with
+// level schedules of the two triangular solves per component.
+struct ImexData {
+  int64_t n_c = 0;
+  std::vector<int64_t> c_dof;          // c index -> lattice DOF (lattice order)
+  std::vector<int64_t> c_of_dof;       // lattice DOF -> c index or -1
+  std::vector<int64_t> ccells;         // kept cells with at least one c-DOF
+  // symmetric pattern of S over c indices (CSR, full) and the two value arrays
+  std::vector<int64_t> Sp, Si;
+  std::vector<double> Mx, Kx;
+  // ordering: permuted row r -> c index, components as contiguous row ranges
+  std::vector<int64_t> perm, iperm;
+  std::vector<int32_t> comp_ptr;
+  // residual gather: permuted row r -> entries (slot * n_loc + loc) into the c-cell products
+  std::vector<int64_t> g_ptr;
+  std::vector<int32_t> g_idx;
+  // factor of S (rebuilt per dt)
+  SparseChol chol;
+  std::vector<int32_t> comp_flvl, comp_blvl;   // per component: range into level pointers
+  double beta_dt2 = 0.0;
+};
+// Build the partition and the pattern (dt-independent part).
+void imex_partition(const Setup& s, ImexData& d);
+// Factor S = M^cc + beta_dt2 K^cc; returns false (with message) if S is not positive definite.
+bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err);
+// Solve M^cc a = b (b and a in c-index order) with a Cholesky factor of M^cc.
+bool imex_mass_solve(const ImexData& d, const std::vector<double>& b, std::vector<double>& a,
+                     std::string& err);
 
 }  // namespace ibfem

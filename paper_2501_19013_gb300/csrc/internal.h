@@ -42,6 +42,43 @@ struct DevProblem {
   unsigned int* done;       // block-completion counter for the step increment
   int* flags;               // bit 0: non-finite state
   int tiles[3];             // tile grid of the fused kernel
+  // mixed-precision tensor-core path
+  int tc_tiles[3];          // tile grid of the tensor-core kernel
+  const float* tc_bimg;     // K_ref as UMMA B operand: hi image then lo image (TF32)
+  const float* minv32;      // dt^2 / M_L in FP32 (0 = dead)
+  const int32_t* tsrc_ptr;  // source CSR over the tensor-core tile grid
+  const int64_t* tsrc_dof;
+  const double* tsrc_val;
+  // IMEX: c-DOF velocity / acceleration (c-index order) and predictor coefficients
+  double* imex_vc;
+  double* imex_ac;
+  double imex_c1;           // (1/2 - beta) dt^2
+  double imex_c2;           // (1 - gamma) dt
+};
+
+// Device view of the IMEX partition and factor (kernels_imex.cu).
+struct ImexDev {
+  int n_cells;               // cells touching the c-set
+  const int64_t* cells;
+  double* Y;                 // n_cells * n_loc products K^e x_e
+  int n_comp;                // connected components = CTAs of the solve
+  const int32_t* comp_ptr;   // permuted-row ranges of the components
+  const int64_t* g_ptr;      // residual gather per permuted row
+  const int32_t* g_idx;
+  const double* Fc;          // spatial load on the c-DOFs (permuted rows), or null
+  double* work;              // n_c
+  const int64_t *Lp, *Li;    // L by rows, diagonal last
+  const double* Lx;
+  const int64_t *Up, *Ui;    // L^T by rows, diagonal first
+  const double* Ux;
+  const double* dinv;        // 1 / L_rr
+  const int32_t *f_lvl, *f_rows, *comp_flvl;
+  const int32_t *b_lvl, *b_rows, *comp_blvl;
+  const int64_t* perm;       // permuted row -> c index
+  const int64_t* c_dof;      // c index -> lattice DOF
+  double* vc;
+  double* ac;
+  double beta_dt2, gamma_dt;
 };
 
 // Input transform of the operator kernels: x_i = in[i] * (vec ? vec[i] : 1) * (scal ? *scal : 1)
@@ -56,16 +93,28 @@ enum OpMode : int {
   kModeStartup = 1,   // out <- u - dt * out + 0.5 minv (F_0 - K u)  (out holds v0)
   kModeApply = 2,     // out <- K x
   kModePower = 3,     // out <- sinv * K x, partial sums of x_in * out and out * out
+  kModeImex = 4,      // d-DOFs: CDM update; c-DOFs: Newmark predictor (no step advance)
 };
 
 // Launchers (kernels_fp64.cu)
-cudaError_t launch_cut_apply_fp64(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st);
+cudaError_t launch_cut_apply_fp64(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st,
+                                  bool do_cut = true);
+// Launchers (kernels_imex.cu)
+cudaError_t launch_imex_cell_apply(const DevProblem& pb, const ImexDev& im, const double* x, cudaStream_t st);
+cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* out, cudaStream_t st);
 cudaError_t launch_op_fp64(const DevProblem& pb, OpInput x, double* out, int mode,
                            double* partials, cudaStream_t st);
 cudaError_t launch_reduce_power(const double* partials, int nblocks, double* lam_hist,
                                 double* inv_norm, int iter, cudaStream_t st);
 cudaError_t launch_sample_now(const DevProblem& pb, const double* u, double* out, cudaStream_t st);
 int op_fp64_blocks(const DevProblem& pb);
+// Launchers (kernels_tc.cu)
+cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int passes,
+                         cudaStream_t st);
+bool op_tc_supported(int dim, int p, int ncomp);
+void op_tc_tiles(int dim, int p, int ncomp, int* tile);
+void op_tc_dims(int dim, int p, int ncomp, int* kp, int* np);
+int op_tc_core_offset(int kp, int row, int k);
 bool op_fp64_supported(int dim, int p, int ncomp);
 void op_fp64_tiles(int dim, int p, int ncomp, int* tile);
 

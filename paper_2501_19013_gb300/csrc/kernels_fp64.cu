@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) op_fp64_kernel(DevProblem pb, OpInput x, 
   double fk = 0.0;
   unsigned long long k = 0;
   int src_lo = 0, src_hi = 0;
-  if (mode == kModeCDM || mode == kModeStartup) {
+  if (mode == kModeCDM || mode == kModeStartup || mode == kModeImex) {
     k = *((volatile unsigned long long*)pb.step);
     if (pb.src_ptr && pb.f_e > 0.0) {
       src_lo = pb.src_ptr[tile];
@@ -254,12 +254,18 @@ __global__ void __launch_bounds__(256) op_fp64_kernel(DevProblem pb, OpInput x, 
           if (pb.src_dof[s2] == dof) f += pb.src_val[s2] * fk;
         double r = f - ku;
         double nv;
-        if (mode == kModeCDM)
-          nv = fma(2.0, uval, -out[dof]) + m * r;
-        else
+        if (mode == kModeStartup)
           nv = uval - pb.dt * out[dof] + 0.5 * m * r;
+        else
+          nv = fma(2.0, uval, -out[dof]) + m * r;
         out[dof] = nv;
         if (!isfinite(nv)) bad = true;
+      } else if (m < 0.0 && mode == kModeImex) {
+        // c-DOF: Newmark predictor of Algorithm 2 (beta = 1/4, gamma = 1/2)
+        int64_t ci = (int64_t)(-m) - 1;
+        double a = pb.imex_ac[ci], v = pb.imex_vc[ci];
+        out[dof] = uval + pb.dt * v + pb.imex_c1 * a;
+        pb.imex_vc[ci] = v + pb.imex_c2 * a;
       }
     }
   }
@@ -360,8 +366,8 @@ static cudaError_t launch_op_t(const DevProblem& pb, OpInput x, double* out, int
 }
 
 template <int D, int P, int N>
-static cudaError_t launch_cut_t(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st) {
-  int ncb = (pb.n_cut + 7) / 8;
+static cudaError_t launch_cut_t(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st, bool do_cut) {
+  int ncb = do_cut ? (pb.n_cut + 7) / 8 : 0;
   int nsb = sample && pb.n_obs_rows > 0 ? (pb.n_obs_rows + 255) / 256 : 0;
   if (ncb + nsb == 0) return cudaSuccess;
   cut_apply_fp64_kernel<D, P, N><<<ncb + nsb, 256, 0, st>>>(pb, x, ncb, sample ? 1 : 0);
@@ -377,9 +383,9 @@ cudaError_t launch_op_fp64(const DevProblem& pb, OpInput x, double* out, int mod
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_cut_apply_fp64(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st) {
+cudaError_t launch_cut_apply_fp64(const DevProblem& pb, OpInput x, bool sample, cudaStream_t st, bool do_cut) {
 #define X(D, P, N) \
-  if (pb.dim == D && pb.p == P && pb.ncomp == N) return launch_cut_t<D, P, N>(pb, x, sample, st);
+  if (pb.dim == D && pb.p == P && pb.ncomp == N) return launch_cut_t<D, P, N>(pb, x, sample, st, do_cut);
   IBFEM_FOR_EACH_SHAPE(X)
 #undef X
   return cudaErrorInvalidValue;

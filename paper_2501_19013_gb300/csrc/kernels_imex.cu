@@ -1,0 +1,140 @@
+// Newmark IMEX step on the GPU (Algorithm 2 of Buerchner et al., arXiv 2501.19013).
+//
+// Per step, after the fused kernel has advanced the d-DOFs explicitly (Eq. cdm) and
+// written the c-DOF predictor Psi_pred^c = Psi^c + dt Psi'^c + (1/2 - beta) dt^2 Psi''^c
+// (and Psi'_pred^c) into the new state buffer:
+//   * imex_cell_apply : y_e = K^e x_e for every cell touching a c-DOF (one warp per cell,
+//                       FP64), x = [Psi_{k+1}^d ; Psi_pred^c];
+//   * imex_solve      : one CTA per connected component of the c-set: the residual
+//                       r = F^c_{k+1} - K^c Psi_pred gathered in a fixed order, the
+//                       level-scheduled forward and backward solves with the host Cholesky
+//                       factor of S = M^cc + beta dt^2 K^cc, and the Newmark correction
+//                       Psi''^c = S^{-1} r, Psi'^c = Psi'_pred^c + gamma dt Psi''^c,
+//                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c.  The last CTA advances the
+//                       step counter.
+#include "internal.h"
+
+namespace ibfem {
+
+__device__ __forceinline__ double ricker_imex(double t, double f_e) {
+  const double pi = 3.141592653589793238462643383279502884;
+  double ts = 2.0 * sqrt(6.0) / (pi * f_e);
+  double q = pi * f_e * (t - ts);
+  return (1.0 - 2.0 * q * q) * exp(-q * q);
+}
+
+template <int DIM, int P, int NC>
+__global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, ImexDev im, const double* __restrict__ x) {
+  constexpr int NN1 = P + 1;
+  constexpr int NL = (DIM == 2 ? NN1 * NN1 : NN1 * NN1 * NN1) * NC;
+  __shared__ double xs[8][NL];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int slot = blockIdx.x * 8 + warp;
+  if (slot >= im.n_cells) return;
+  int64_t cell = im.cells[slot];
+  int cx = (int)(cell % pb.n[0]);
+  int cy = (int)((cell / pb.n[0]) % pb.n[1]);
+  int cz = DIM == 3 ? (int)(cell / ((int64_t)pb.n[0] * pb.n[1])) : 0;
+  for (int j = lane; j < NL; j += 32) {
+    int node = j / NC, comp = j % NC;
+    int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
+    int64_t g = ((int64_t)(cz * P + c) * pb.lat[1] + (cy * P + b)) * pb.lat[0] + cx * P + a;
+    xs[warp][j] = x[g * NC + comp];
+  }
+  __syncwarp();
+  const double* K = pb.cls[cell] == 1 ? pb.Kcut + (size_t)pb.cut_index[cell] * NL * NL : pb.Kref;
+  for (int i = lane; i < NL; i += 32) {
+    double acc = 0.0;
+    for (int j = 0; j < NL; ++j) acc = fma(K[(size_t)j * NL + i], xs[warp][j], acc);
+    im.Y[(size_t)slot * NL + i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(1024) imex_solve_kernel(DevProblem pb, ImexDev im, double* __restrict__ out) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int r0 = im.comp_ptr[b], r1 = im.comp_ptr[b + 1];
+  const unsigned long long k = *((volatile unsigned long long*)pb.step);
+  double fk1 = 0.0;
+  if (pb.f_e > 0.0 && im.Fc) fk1 = ricker_imex((double)(k + 1) * pb.dt, pb.f_e);
+  double* w = im.work;
+  // residual r = F_{k+1}^c - K^c Psi_pred (fixed summation order)
+  for (int r = r0 + tid; r < r1; r += blockDim.x) {
+    double acc = im.Fc ? im.Fc[r] * fk1 : 0.0;
+    for (int64_t e = im.g_ptr[r]; e < im.g_ptr[r + 1]; ++e) acc -= im.Y[im.g_idx[e]];
+    w[r] = acc;
+  }
+  __syncthreads();
+  // L y = r, level by level
+  for (int lv = im.comp_flvl[b]; lv < im.comp_flvl[b + 1]; ++lv) {
+    for (int q = im.f_lvl[lv] + warp; q < im.f_lvl[lv + 1]; q += nwarps) {
+      int r = im.f_rows[q];
+      int64_t p0 = im.Lp[r], p1 = im.Lp[r + 1] - 1;  // diagonal stored last
+      double acc = 0.0;
+      for (int64_t p = p0 + lane; p < p1; p += 32) acc = fma(im.Lx[p], w[im.Li[p]], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) w[r] = (w[r] - acc) * im.dinv[r];
+    }
+    __syncthreads();
+  }
+  // L^T x = y, level by level
+  for (int lv = im.comp_blvl[b]; lv < im.comp_blvl[b + 1]; ++lv) {
+    for (int q = im.b_lvl[lv] + warp; q < im.b_lvl[lv + 1]; q += nwarps) {
+      int r = im.b_rows[q];
+      int64_t p0 = im.Up[r] + 1, p1 = im.Up[r + 1];  // diagonal stored first
+      double acc = 0.0;
+      for (int64_t p = p0 + lane; p < p1; p += 32) acc = fma(im.Ux[p], w[im.Ui[p]], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) w[r] = (w[r] - acc) * im.dinv[r];
+    }
+    __syncthreads();
+  }
+  // Newmark correction on the c-DOFs
+  bool bad = false;
+  for (int r = r0 + tid; r < r1; r += blockDim.x) {
+    int64_t ci = im.perm[r];
+    double a = w[r];
+    im.ac[ci] = a;
+    im.vc[ci] = fma(im.gamma_dt, a, im.vc[ci]);
+    int64_t dof = im.c_dof[ci];
+    double nv = fma(im.beta_dt2, a, out[dof]);
+    out[dof] = nv;
+    if (!isfinite(nv)) bad = true;
+  }
+  if (bad) atomicOr(pb.flags, 1);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    unsigned prev = atomicAdd(pb.done, 1u);
+    if (prev == gridDim.x - 1) {
+      *pb.step = k + 1;
+      *pb.done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+#define IBFEM_IMEX_SHAPES(X) \
+  X(2, 1, 1) X(2, 2, 1) X(2, 3, 1) X(2, 4, 1) X(2, 5, 1) X(2, 6, 1) \
+  X(2, 1, 2) X(2, 2, 2) X(2, 3, 2) X(2, 4, 2) X(3, 1, 1) X(3, 2, 1) X(3, 3, 1)
+
+cudaError_t launch_imex_cell_apply(const DevProblem& pb, const ImexDev& im, const double* x, cudaStream_t st) {
+  if (im.n_cells == 0) return cudaSuccess;
+  int blocks = (im.n_cells + 7) / 8;
+#define X(D, P, N)                                                                   \
+  if (pb.dim == D && pb.p == P && pb.ncomp == N) {                                   \
+    imex_cell_apply_kernel<D, P, N><<<blocks, 256, 0, st>>>(pb, im, x);              \
+    return cudaGetLastError();                                                       \
+  }
+  IBFEM_IMEX_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* out, cudaStream_t st) {
+  if (im.n_comp == 0) return cudaSuccess;
+  imex_solve_kernel<<<im.n_comp, 1024, 0, st>>>(pb, im, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ibfem

@@ -115,9 +115,32 @@ void Handle::build_device() {
       minv[i] = 1.0 / s.ML[i];
       sinv[i] = 1.0 / std::sqrt(s.ML[i]);
     }
+  if (imex)
+    for (int64_t ci = 0; ci < imex_host.n_c; ++ci) sinv[imex_host.c_dof[ci]] = 0.0;  // d-block only
   d_minv = upload(minv);
   pb.minv = d_minv;
   pb.sinv = upload(sinv);
+  if (imex) {
+    const ImexData& I = imex_host;
+    ImexDev& D = imex_dev;
+    std::memset(&D, 0, sizeof(D));
+    D.n_cells = (int)I.ccells.size();
+    D.cells = upload(I.ccells);
+    D.Y = static_cast<double*>(dalloc(std::max<size_t>(I.ccells.size(), 1) * s.n_loc * sizeof(double)));
+    D.n_comp = (int)I.comp_ptr.size() - 1;
+    D.comp_ptr = upload(I.comp_ptr);
+    D.g_ptr = upload(I.g_ptr);
+    D.g_idx = upload(I.g_idx);
+    D.work = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
+    D.perm = upload(I.perm);
+    D.c_dof = upload(I.c_dof);
+    D.vc = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
+    D.ac = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
+    check(cudaMemsetAsync(D.vc, 0, I.n_c * sizeof(double), stream), "memset");
+    check(cudaMemsetAsync(D.ac, 0, I.n_c * sizeof(double), stream), "memset");
+    pb.imex_vc = D.vc;
+    pb.imex_ac = D.ac;
+  }
   for (int b = 0; b < 2; ++b) {
     U[b] = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
     check(cudaMemsetAsync(U[b], 0, s.n_lat_dof * sizeof(double), stream), "memset");
@@ -133,10 +156,77 @@ void Handle::build_device() {
   for (int k = 0; k < 3; ++k) pb.tiles[k] = k < s.dim ? (s.n[k] + tile[k] - 1) / tile[k] : 1;
   n_blocks = op_fp64_blocks(pb);
   partials = static_cast<double*>(dalloc(2 * (size_t)n_blocks * sizeof(double)));
+  if (opt.precision != IBFEM_FP64) {
+    // K_ref as the UMMA B operand (row i = K_ref[i, :], K-major core matrices), TF32 hi/lo
+    int kp = 0, np = 0;
+    op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
+    std::vector<float> img(2 * (size_t)np * kp, 0.f);
+    for (int i = 0; i < np; ++i)
+      for (int j = 0; j < kp; ++j) {
+        double v = (i < s.n_loc && j < s.n_loc) ? s.Kref[(size_t)i * s.n_loc + j] : 0.0;
+        float f = (float)v;
+        uint32_t b;
+        std::memcpy(&b, &f, 4);
+        b &= 0xFFFFE000u;
+        float hi;
+        std::memcpy(&hi, &b, 4);
+        float lo = (float)(v - (double)hi);
+        int o = op_tc_core_offset(kp, i, j);
+        img[o] = hi;
+        img[(size_t)np * kp + o] = lo;
+      }
+    pb.tc_bimg = upload(img);
+    std::vector<float> k32(s.Kcut.begin(), s.Kcut.end());
+    pb.Kcut32 = upload(k32);
+    std::vector<float> m32(s.n_lat_dof, 0.f);
+    for (int64_t i = 0; i < s.n_lat_dof; ++i)
+      if (s.ML[i] > 0) m32[i] = (float)(1.0 / s.ML[i]);
+    d_minv32 = upload(m32);
+    pb.minv32 = d_minv32;
+    op_tc_tiles(s.dim, s.p, s.ncomp, tc_tile);
+    for (int k = 0; k < 3; ++k) pb.tc_tiles[k] = k < s.dim ? (s.n[k] + tc_tile[k] - 1) / tc_tile[k] : 1;
+  }
   scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
   lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
   scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
   check(cudaStreamSynchronize(stream), "setup sync");
+}
+
+void Handle::imex_upload_factor() {
+  const ImexData& I = imex_host;
+  const SparseChol& L = I.chol;
+  ImexDev& D = imex_dev;
+  size_t nnz = L.Lx.size();
+  if (imex_nnz_alloc != nnz) {
+    // the pattern and order do not depend on dt: allocated once
+    D.Lp = static_cast<int64_t*>(dalloc((I.n_c + 1) * sizeof(int64_t)));
+    D.Li = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t)));
+    D.Lx = static_cast<double*>(dalloc(nnz * sizeof(double)));
+    D.Up = static_cast<int64_t*>(dalloc((I.n_c + 1) * sizeof(int64_t)));
+    D.Ui = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t)));
+    D.Ux = static_cast<double*>(dalloc(nnz * sizeof(double)));
+    D.dinv = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
+    D.f_lvl = upload(L.fwd_level_ptr);
+    D.f_rows = upload(L.fwd_rows);
+    D.b_lvl = upload(L.bwd_level_ptr);
+    D.b_rows = upload(L.bwd_rows);
+    D.comp_flvl = upload(I.comp_flvl);
+    D.comp_blvl = upload(I.comp_blvl);
+    imex_nnz_alloc = nnz;
+  }
+  std::vector<double> dinv(I.n_c);
+  for (int64_t r = 0; r < I.n_c; ++r) dinv[r] = 1.0 / L.Ux[L.Up[r]];
+  auto cp = [&](const void* dst, const void* src, size_t bytes) {
+    check(cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, stream), "factor upload");
+  };
+  cp(D.Lp, L.Lp.data(), L.Lp.size() * sizeof(int64_t));
+  cp(D.Li, L.Li.data(), nnz * sizeof(int64_t));
+  cp(D.Lx, L.Lx.data(), nnz * sizeof(double));
+  cp(D.Up, L.Up.data(), L.Up.size() * sizeof(int64_t));
+  cp(D.Ui, L.Ui.data(), nnz * sizeof(int64_t));
+  cp(D.Ux, L.Ux.data(), nnz * sizeof(double));
+  cp(D.dinv, dinv.data(), dinv.size() * sizeof(double));
+  check(cudaStreamSynchronize(stream), "factor upload");
 }
 
 void Handle::invalidate_graphs() {
@@ -184,6 +274,37 @@ void Handle::timed_collect() {
 
 // One CDM step with u = U[cur], out = U[1 - cur] (in place over u^{k-1}).
 void Handle::enqueue_step(int cur) {
+  if (opt.precision != IBFEM_FP64) {
+    slot_name[1] = opt.precision == IBFEM_TF32X3_TC ? "op_tc_tf32x3_fused_cdm" : "op_tc_tf32_fused_cdm";
+    if (timing) step_first_ev.push_back(ev_used);
+    timed_begin(1);
+    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_passes(), stream), "op_tc");
+    timed_end();
+    if (timing) step_last_ev.push_back(ev_used - 1);
+    return;
+  }
+  if (imex) {
+    OpInput x{U[cur], nullptr, nullptr};
+    slot_name[1] = "observers";
+    slot_name[2] = "op_fp64_fused_imex_explicit";
+    slot_name[3] = "imex_cell_apply";
+    slot_name[4] = "imex_solve";
+    if (timing) step_first_ev.push_back(ev_used);
+    timed_begin(1);
+    check(launch_cut_apply_fp64(dev, x, true, stream, false), "observers");
+    timed_end();
+    timed_begin(2);
+    check(launch_op_fp64(dev, x, U[1 - cur], kModeImex, nullptr, stream), "op_imex");
+    timed_end();
+    timed_begin(3);
+    check(launch_imex_cell_apply(dev, imex_dev, U[1 - cur], stream), "imex_cells");
+    timed_end();
+    timed_begin(4);
+    check(launch_imex_solve(dev, imex_dev, U[1 - cur], stream), "imex_solve");
+    timed_end();
+    if (timing) step_last_ev.push_back(ev_used - 1);
+    return;
+  }
   OpInput x{U[cur], nullptr, nullptr};
   slot_name[1] = "cut_apply_fp64";
   slot_name[2] = "op_fp64_fused_cdm";
@@ -282,8 +403,15 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   if (!(alpha >= 0.0)) throw std::invalid_argument("alpha must be >= 0");
   if (o.physics != IBFEM_SCALAR && o.physics != IBFEM_ELASTIC_PLANE_STRAIN)
     throw std::invalid_argument("unknown physics");
-  if (o.scheme != IBFEM_CDM) throw std::invalid_argument("scheme not supported by this build");
-  if (o.precision != IBFEM_FP64) throw std::invalid_argument("precision not supported by this build");
+  if (o.scheme != IBFEM_CDM && o.scheme != IBFEM_IMEX) throw std::invalid_argument("unknown scheme");
+  if (o.scheme == IBFEM_IMEX && o.precision != IBFEM_FP64)
+    throw std::invalid_argument("IMEX runs in FP64 (precision must be IBFEM_FP64)");
+  in.need_consistent_mass = o.scheme == IBFEM_IMEX;
+  if (o.precision != IBFEM_FP64 && o.precision != IBFEM_TF32X3_TC && o.precision != IBFEM_TF32_TC)
+    throw std::invalid_argument("precision not supported by this build");
+  if (o.precision != IBFEM_FP64 && !o.host_only &&
+      !op_tc_supported(grid->dim, p, o.physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1))
+    throw std::invalid_argument("no tensor-core kernel instantiation for this (dim, p, ncomp)");
   if (!(o.rho > 0)) throw std::invalid_argument("rho must be > 0");
   if (stab) {
     in.stab = stab->kind;
@@ -319,6 +447,10 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   if (!o.host_only && !op_fp64_supported(in.dim, in.p, in.physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1))
     throw std::invalid_argument("no kernel instantiation for this (dim, p, ncomp)");
   h->setup = build_setup(in);
+  if (o.scheme == IBFEM_IMEX) {
+    imex_partition(h->setup, h->imex_host);
+    h->imex = h->imex_host.n_c > 0;   // without cut cells IMEX is the CDM
+  }
   if (!o.host_only) {
     check(cudaSetDevice(o.device), "cudaSetDevice");
     h->stream = static_cast<cudaStream_t>(o.stream);
@@ -365,6 +497,11 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
   out->dt = h->dt;
   out->t = h->step * h->dt;
   out->lambda_ref = s.lambda_ref;
+  if (h->imex) {
+    out->n_c = h->imex_host.n_c;
+    out->nnz_L = (int64_t)h->imex_host.chol.Lx.size();
+    out->n_levels = (int32_t)h->imex_host.chol.fwd_level_ptr.size() - 1;
+  }
   out->device_bytes = h->device_bytes;
   return IBFEM_OK;
 }
@@ -424,6 +561,20 @@ int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, do
     if (!merged.empty() && merged.back().first == e.first) merged.back().second += e.second;
     else merged.push_back(e);
   }
+  h->src_host = merged;
+  h->src_fe = kind == IBFEM_SRC_NONE ? 0.0 : f_e;
+  if (h->imex) {
+    std::vector<double> fc(h->imex_host.n_c, 0.0);
+    bool any = false;
+    for (auto& e : merged) {
+      int64_t ci = h->imex_host.c_of_dof[e.first];
+      if (ci >= 0) {
+        fc[h->imex_host.iperm[ci]] += e.second;
+        any = true;
+      }
+    }
+    h->imex_dev.Fc = any ? h->upload(fc) : nullptr;
+  }
   int ntiles = h->n_blocks;
   std::vector<std::vector<std::pair<int64_t, double>>> per(ntiles);
   for (auto& e : merged) {
@@ -452,6 +603,35 @@ int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, do
   h->dev.src_ptr = h->upload(ptr);
   h->dev.src_dof = h->upload(sd);
   h->dev.src_val = h->upload(sv);
+  if (h->opt.precision != IBFEM_FP64) {
+    int nt = h->dev.tc_tiles[0] * h->dev.tc_tiles[1] * h->dev.tc_tiles[2];
+    std::vector<std::vector<std::pair<int64_t, double>>> per2(nt);
+    for (auto& e : merged) {
+      int64_t rem = e.first / s.ncomp;
+      int t = 0, stride = 1;
+      for (int k = 0; k < s.dim; ++k) {
+        int64_t g = rem % s.lat[k];
+        rem /= s.lat[k];
+        int b = (int)std::min<int64_t>(g / ((int64_t)h->tc_tile[k] * s.p), h->dev.tc_tiles[k] - 1);
+        t += b * stride;
+        stride *= h->dev.tc_tiles[k];
+      }
+      per2[t].push_back(e);
+    }
+    std::vector<int32_t> p2(nt + 1, 0);
+    std::vector<int64_t> d2;
+    std::vector<double> v2;
+    for (int t = 0; t < nt; ++t) {
+      for (auto& e : per2[t]) {
+        d2.push_back(e.first);
+        v2.push_back(e.second);
+      }
+      p2[t + 1] = (int32_t)d2.size();
+    }
+    h->dev.tsrc_ptr = h->upload(p2);
+    h->dev.tsrc_dof = h->upload(d2);
+    h->dev.tsrc_val = h->upload(v2);
+  }
   h->dev.f_e = kind == IBFEM_SRC_NONE ? 0.0 : f_e;
   h->invalidate_graphs();
   check(cudaStreamSynchronize(h->stream), "source upload");
@@ -503,7 +683,24 @@ int ibfem_set_dt(ibfem_t* h, double dt) {
   std::vector<double> minv(s.n_lat_dof, 0.0);
   for (int64_t i = 0; i < s.n_lat_dof; ++i)
     if (s.ML[i] > 0) minv[i] = dt * dt / s.ML[i];
+  if (h->imex) {
+    // c-DOFs carry -(c + 1): the fused kernel then forms the Newmark predictor there
+    for (int64_t ci = 0; ci < h->imex_host.n_c; ++ci) minv[h->imex_host.c_dof[ci]] = -(double)(ci + 1);
+    std::string err;
+    const double beta = 0.25, gamma = 0.5;
+    if (!imex_factor(s, beta * dt * dt, h->imex_host, err)) throw std::runtime_error("IMEX factorisation: " + err);
+    h->imex_upload_factor();
+    h->imex_dev.beta_dt2 = beta * dt * dt;
+    h->imex_dev.gamma_dt = gamma * dt;
+    h->dev.imex_c1 = (0.5 - beta) * dt * dt;
+    h->dev.imex_c2 = (1.0 - gamma) * dt;
+  }
   check(cudaMemcpyAsync(h->d_minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "minv");
+  std::vector<float> m32;
+  if (h->d_minv32) {
+    m32.assign(minv.begin(), minv.end());
+    check(cudaMemcpyAsync(h->d_minv32, m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream), "minv32");
+  }
   check(cudaStreamSynchronize(h->stream), "set_dt");
   h->dt = dt;
   h->dev.dt = dt;
@@ -528,6 +725,43 @@ int ibfem_set_initial(ibfem_t* h, const double* u0, const double* v0) {
   OpInput x{h->U[0], nullptr, nullptr};
   check(launch_cut_apply_fp64(h->dev, x, false, h->stream), "cut_apply");
   check(launch_op_fp64(h->dev, x, h->U[1], kModeStartup, nullptr, h->stream), "startup");
+  if (h->imex) {
+    // Psi'_0 on c and Psi''_0 = (M^cc)^{-1} (F_0^c - K^c Psi_0) (Algorithm 2, initialisation)
+    const Setup& s = h->setup;
+    const ImexData& I = h->imex_host;
+    const int nl = s.n_loc, nc = s.ncomp;
+    std::vector<double> rhs(I.n_c, 0.0), vc(I.n_c, 0.0), ac;
+    for (auto& e : h->src_host) {
+      int64_t ci = I.c_of_dof[e.first];
+      if (ci >= 0 && h->src_fe > 0) {
+        const double pi = 3.141592653589793238462643383279502884;
+        double ts = 2.0 * std::sqrt(6.0) / (pi * h->src_fe), q = pi * h->src_fe * (0.0 - ts);
+        rhs[ci] += e.second * (1.0 - 2.0 * q * q) * std::exp(-q * q);
+      }
+    }
+    std::vector<double> xe(nl);
+    std::vector<int64_t> dofs(nl);
+    for (int64_t e : I.ccells) {
+      for (int l = 0; l < s.nn_loc; ++l)
+        for (int c = 0; c < nc; ++c) {
+          dofs[l * nc + c] = lattice_node(s, e, l) * nc + c;
+          xe[l * nc + c] = lu[dofs[l * nc + c]];
+        }
+      const double* K = s.cls[e] == kCut ? &s.Kcut[(size_t)s.cut_index[e] * nl * nl] : s.Kref.data();
+      for (int a = 0; a < nl; ++a) {
+        int64_t ci = I.c_of_dof[dofs[a]];
+        if (ci < 0) continue;
+        double acc = 0.0;
+        for (int b = 0; b < nl; ++b) acc += K[(size_t)a * nl + b] * xe[b];
+        rhs[ci] -= acc;
+      }
+    }
+    for (int64_t ci = 0; ci < I.n_c; ++ci) vc[ci] = lv[I.c_dof[ci]];
+    std::string err;
+    if (!imex_mass_solve(I, rhs, ac, err)) throw std::runtime_error("IMEX mass solve: " + err);
+    check(cudaMemcpyAsync(h->imex_dev.vc, vc.data(), vc.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "vc");
+    check(cudaMemcpyAsync(h->imex_dev.ac, ac.data(), ac.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ac");
+  }
   check(cudaStreamSynchronize(h->stream), "set_initial");
   h->step = 0;
   h->ring_start = 0;
@@ -672,8 +906,12 @@ int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
   h->to_lattice(x, lx);
   check(cudaMemcpyAsync(h->W, lx.data(), lx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "x");
   OpInput in{h->W, nullptr, nullptr};
-  check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
-  check(launch_op_fp64(h->dev, in, h->scratch, kModeApply, nullptr, h->stream), "apply");
+  if (h->opt.precision != IBFEM_FP64) {
+    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_passes(), h->stream), "apply_tc");
+  } else {
+    check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
+    check(launch_op_fp64(h->dev, in, h->scratch, kModeApply, nullptr, h->stream), "apply");
+  }
   check(cudaMemcpyAsync(lx.data(), h->scratch, lx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "y");
   check(cudaStreamSynchronize(h->stream), "apply sync");
   h->from_lattice(lx, y);
@@ -693,6 +931,10 @@ int ibfem_crit_dt(ibfem_t* h, int max_iter, double rtol, double* dt_crit, double
   double nrm = 0;
   for (int64_t i = 0; i < s.n_dof; ++i) {
     v[i] = 1.0 + 0.5 * std::sin((double)i);
+    if (h->imex) {
+      int64_t lat = s.lat_of_kept[i / s.ncomp] * s.ncomp + i % s.ncomp;
+      if (h->imex_host.c_of_dof[lat] >= 0) v[i] = 0.0;   // explicit (d) block only
+    }
     nrm += v[i] * v[i];
   }
   nrm = std::sqrt(nrm);

@@ -28,6 +28,17 @@ struct Handle {
   double* W = nullptr;                 // work vector (power iteration, apply)
   double* scratch = nullptr;
   double* d_minv = nullptr;
+  float* d_minv32 = nullptr;
+  int tc_tile[3] = {1, 1, 1};
+  int tc_passes() const { return opt.precision == IBFEM_TF32X3_TC ? 3 : 1; }
+  // IMEX (Algorithm 2): host partition/factor and their device copies
+  bool imex = false;
+  ImexData imex_host;
+  ImexDev imex_dev{};
+  size_t imex_nnz_alloc = 0;
+  std::vector<std::pair<int64_t, double>> src_host;  // merged (lattice dof, value) of the load
+  double src_fe = 0.0;
+  void imex_upload_factor();
   double* partials = nullptr;
   double* scalars = nullptr;
   double* lam_hist = nullptr;

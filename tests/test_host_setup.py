@@ -61,3 +61,12 @@ def test_rotated_cube_dofs_table3(p, ne, dofs):
     s = ib.Solver(3, (ne, ne, ne), p, lo=(0, 0, 0), hi=(0.5, 0.5, 0.5), rotated_box=rb,
                   quad_depth=0, host_only=True)
     assert s.info().n_dof == dofs
+
+
+def test_imex_partition_size():
+    """c-set = DOFs with support in a cut cell (Sec. 2.6)."""
+    w = W.plate_holes_imex(n=30, p=3, count=3, seed=2)
+    d = OD.from_workload(w)
+    s = ib.from_workload(w, host_only=True)
+    assert s.info().n_c == len(d.c_dofs())
+    s.close()
