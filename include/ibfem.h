@@ -60,10 +60,12 @@ enum { IBFEM_SCALAR = 0, IBFEM_ELASTIC_PLANE_STRAIN = 1 };
 enum { IBFEM_CDM = 0, IBFEM_IMEX = 1 };
 /* Precision of the element contractions.  The integrator state (u^k, u^{k-1}), the
  * central-difference update, the IMEX solves and the power iteration are FP64 always. */
-enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores                  */
-       IBFEM_TF32X3_TC = 1,     /* tcgen05 kind::tf32, 3-pass split (about FP32)        */
-       IBFEM_TF32_TC = 2,       /* tcgen05 kind::tf32, one pass                         */
-       IBFEM_BF16_TC = 3        /* tcgen05 kind::f16 with BF16 operands, FP32 accum     */ };
+enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores                      */
+       IBFEM_EXACT_TC = 1,      /* tcgen05 kind::f16, balanced 8-bit digit slices of u and
+                                   K_ref (BF16) accumulated exactly per level (10 MMA chains),
+                                   level 0 assembled in FP64: about 32 significant bits      */
+       IBFEM_BF16X3_TC = 2,     /* tcgen05 kind::f16, BF16 hi/lo splits, 3 passes, FP32 acc. */
+       IBFEM_BF16_TC = 3        /* tcgen05 kind::f16, one BF16 pass, FP32 accumulation      */ };
 enum { IBFEM_SRC_NONE = 0,
        IBFEM_SRC_POINT = 1,          /* params: x, y[, z] [, dir_x, dir_y] (elastic)   */
        IBFEM_SRC_EDGE_TRACTION = 2   /* params: y0, y1, t_x[, t_y]; edge x = lo_x (2D) */ };
@@ -100,7 +102,7 @@ typedef struct {
     double rho, c;            /* density, wave speed (scalar)                          */
     double E, nu;             /* Young's modulus, Poisson ratio (elastic)              */
     int scheme;               /* IBFEM_CDM or IBFEM_IMEX                               */
-    int precision;            /* IBFEM_FP64 / _TF32X3_TC / _TF32_TC / _BF16_TC         */
+    int precision;            /* IBFEM_FP64 / _EXACT_TC / _BF16X3_TC / _BF16_TC         */
     void* stream;             /* cudaStream_t to run on, NULL = the legacy stream      */
     void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator         */
     void (*dev_free)(void* ptr, void* ctx);

@@ -20,7 +20,7 @@ struct DevProblem {
   int n_cut;
   const double* Kref;       // n_loc^2 (symmetric)
   const double* Kcut;       // n_cut * n_loc^2 (symmetric, row-major)
-  const float* Kcut32;      // same in FP32 (mixed precision), may be null
+  const float* Kcut32;      // per cut cell: FP32 hi slice then lo slice (n_loc^2 each)
   double* Ycut;             // n_cut * n_loc: K^e x_e of the cut cells for the current step
   const double* minv;       // dt^2 / M_L per lattice DOF (0 = dead); -(c + 1) marks IMEX c-DOF c
   const double* sinv;       // 1 / sqrt(M_L) per lattice DOF (0 = dead or IMEX c-DOF)
@@ -44,8 +44,9 @@ struct DevProblem {
   int tiles[3];             // tile grid of the fused kernel
   // mixed-precision tensor-core path
   int tc_tiles[3];          // tile grid of the tensor-core kernel
-  const float* tc_bimg;     // K_ref as UMMA B operand: hi image then lo image (TF32)
-  const float* minv32;      // dt^2 / M_L in FP32 (0 = dead)
+  const uint16_t* tc_bimg;  // K_ref as UMMA B operand: four BF16 slices (digits or hi/lo)
+  const int* tc_frow;       // exact scheme: unbiased exponent F_i of each K_ref row
+  const float* minv32;      // dt^2 / M_L as two FP32 slices: hi[n_lat_dof] then lo[n_lat_dof]
   const int32_t* tsrc_ptr;  // source CSR over the tensor-core tile grid
   const int64_t* tsrc_dof;
   const double* tsrc_val;
@@ -109,7 +110,8 @@ cudaError_t launch_reduce_power(const double* partials, int nblocks, double* lam
 cudaError_t launch_sample_now(const DevProblem& pb, const double* u, double* out, cudaStream_t st);
 int op_fp64_blocks(const DevProblem& pb);
 // Launchers (kernels_tc.cu)
-cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int passes,
+// scheme: 0 exact digit slices, 1 bf16 hi/lo three-pass, 2 bf16 one pass
+cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme,
                          cudaStream_t st);
 bool op_tc_supported(int dim, int p, int ncomp);
 void op_tc_tiles(int dim, int p, int ncomp, int* tile);

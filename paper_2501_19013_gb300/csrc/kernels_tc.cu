@@ -1,22 +1,30 @@
-// Mixed-precision element operator on the 5th-generation tensor cores, fused with the
-// FP64 central-difference update (Eq. cdm of Buerchner et al., arXiv 2501.19013).
+// Tensor-core element operator fused with the FP64 central-difference update
+// (Eq. cdm of Buerchner et al., arXiv 2501.19013), for sm_103a (tcgen05 + TMEM).
 //
 // One CTA per tile of cells; it owns the lattice nodes of its tile and recomputes the
-// one-cell halo (as the FP64 kernel), so each node's sum over its cells is formed once, in
-// a fixed order, without atomics.  Per CTA:
-//   1. the FP64 node patch of u^k is read into shared memory;
-//   2. the gathered element vectors X (one row per halo'd cell, M = 128 rows) are split
-//      into TF32 hi/lo parts directly from the FP64 bit patterns (integer ops only) and
-//      stored in the no-swizzle K-major core-matrix layout of a UMMA operand;
-//   3. one thread issues tcgen05.mma kind::tf32: Y = X K_ref^T with the shared reference
-//      matrix K_ref (hi/lo image prepared on the host) -- three passes hi*hi + hi*lo + lo*hi
-//      for about FP32 accuracy, or one pass -- accumulating in TMEM (FP32);
-//   4. four warps drain TMEM with tcgen05.ld into a shared FP32 buffer; cut cells replace
-//      their rows with K^e x_e from their own FP32 matrices (CUDA cores);
-//   5. per owned DOF: (K u)_i = sum of its cells' rows (FP32), delta = (dt^2/m_i)(F_i - (Ku)_i)
-//      in FP32, widened to FP64 by bit manipulation, and u^{k+1} = (2 u^k - u^{k-1}) + delta
-//      in FP64 -- two FP64 operations per DOF, the minimum for an FP64 state update.
-// Block 0 also records the observer readings of u^k; the last block advances the step.
+// one-cell halo, so each node's sum over its cells is formed once, in a fixed order,
+// without atomics.  The uncut cells of the tile (one row of the MMA per halo'd cell,
+// M = 128) are contracted with the shared reference matrix K_ref on the tensor cores:
+//
+//   exact scheme (IBFEM_EXACT_TC) -- an exact-slice (Ozaki-type) product:
+//     x_mj = 2^(E_m - 31) sum_s d_s 2^(24 - 8 s),  K_ij = 2^(F_i - 31) sum_t c_t 2^(24 - 8 t)
+//     with balanced 8-bit digits d_s, c_t (|digit| <= 256, exact in BF16), E_m the row's
+//     largest exponent and F_i the K row's.  Products of digits accumulate EXACTLY in the
+//     FP32 accumulators of tcgen05.mma kind::f16 (integers below 2^24), one TMEM accumulator
+//     per level l = s + t <= 3 (10 MMA chains).  Level 0 goes to FP64 exactly; levels 1-3
+//     are combined in FP32 (they are 2^-8 smaller).  The node sums of level 0 are formed in
+//     FP64, so the cancellation in K u (element products ~ lambda_max |u|, the sum much
+//     smaller) costs no precision; the result carries about 32 significant bits.
+//   bf16x3 / bf16 -- hi/lo BF16 splits with three MMA passes (hi.hi + hi.lo + lo.hi), or one
+//     pass, accumulated in FP32 (the plain mixed-precision contraction).
+//
+// Cut cells replace their rows with K^e x_e computed on the CUDA cores in double-FP32
+// arithmetic (two-slice FP32 matrices, error-free products and sums).  Per owned DOF:
+// (K u)_i = hi (FP64) + lo (FP32), r = F_i - K u (FP32 after the FP64 cancellation),
+// delta = (dt^2/m_i) r with a two-slice FP32 dt^2/m, widened to FP64 by bit manipulation,
+// and u^{k+1} = (2 u^k - u^{k-1}) + delta in FP64: two FP64 operations per DOF plus one per
+// extra cell sharing the node, the only FP64 arithmetic of the step.
+// The K_ref digit image is copied into shared memory with the bulk-async (TMA) engine.
 #include <cstdint>
 
 #include "internal.h"
@@ -29,35 +37,43 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// FP64 -> FP32 by truncating the significand (integer pipe only; values below the FP32
-// normal range flush to zero, above it saturate to infinity).
-__device__ __forceinline__ uint32_t f64_to_f32_bits(double x) {
+// FP32 -> FP64 exactly by bit manipulation with an extra power-of-two scale 2^sh
+// (integer pipe only; zero and subnormal inputs give zero).
+__device__ __forceinline__ double f32_to_f64_scaled(float f, int sh) {
+  uint32_t b = __float_as_uint(f);
+  int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0.0;
+  uint32_t sign = b & 0x80000000u, m = b & 0x7fffffu;
+  int e64 = e + 896 + sh;
+  if (e64 <= 0) return 0.0;                                   // below FP64 normals: negligible
+  if (e64 >= 2047) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
+  uint32_t hi = sign | ((uint32_t)e64 << 20) | (m >> 3);
+  uint32_t lo = m << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// f * 2^sh in FP32 by exponent arithmetic (flush to zero on underflow)
+__device__ __forceinline__ float f32_scale(float f, int sh) {
+  uint32_t b = __float_as_uint(f);
+  int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0.f;
+  int e2 = e + sh;
+  if (e2 <= 0) return 0.f;
+  if (e2 >= 255) return __uint_as_float((b & 0x80000000u) | 0x7f800000u);
+  return __uint_as_float((b & 0x807fffffu) | ((uint32_t)e2 << 23));
+}
+
+// FP64 -> FP32 rounding to nearest by bit manipulation (ties away from zero).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
   uint32_t sign = hi & 0x80000000u;
   int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  if (e <= 0) return sign;
-  if (e >= 255) return sign | 0x7f800000u;
-  return sign | ((uint32_t)e << 23) | m;
-}
-
-// FP32 -> FP64 exactly by bit manipulation (subnormals flush to zero).
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  uint32_t b = __float_as_uint(f);
-  uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  uint32_t hi, lo;
-  if (e == 0) {
-    hi = sign;
-    lo = 0;
-  } else if (e == 255) {
-    hi = sign | 0x7ff00000u | (m >> 3);
-    lo = m << 29;
-  } else {
-    hi = sign | ((e + 896u) << 20) | (m >> 3);
-    lo = m << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  uint32_t r = ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  r += (lo >> 28) & 1u;  // carry may bump the exponent: still correct
+  return __uint_as_float(sign | r);
 }
 
 __device__ __forceinline__ double ricker_tc(double t, double f_e) {
@@ -75,9 +91,52 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
+__device__ __forceinline__ uint16_t bf16_of_small_int(int v) {
+  // |v| <= 256 has at most 8 significant bits: the upper half of its FP32 pattern is exact
+  return (uint16_t)(__float_as_uint((float)v) >> 16);
+}
+
+__device__ __forceinline__ uint16_t bf16_rn(float f) {
+  uint32_t b = __float_as_uint(f);
+  b += 0x7fffu + ((b >> 16) & 1u);  // round to nearest even (finite inputs)
+  return (uint16_t)(b >> 16);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (int it = 0; it < (1 << 24) && !ok; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// error-free transformations of double-FP32 arithmetic
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+constexpr int kNoScale = -100000;  // E_m marker: rows whose (D0, L) are already scaled
+
 }  // namespace
 
-// Tile geometry of the tensor-core kernel (halo'd cells <= 128 = M).
 __host__ __device__ constexpr int tc_tile_x(int dim, int nl) { return dim == 3 ? 4 : (nl >= 32 ? 8 : 15); }
 __host__ __device__ constexpr int tc_tile_y(int dim, int nl) { return dim == 3 ? 4 : (nl >= 32 ? 8 : 7); }
 __host__ __device__ constexpr int tc_tile_z(int dim) { return dim == 3 ? 4 : 1; }
@@ -87,54 +146,65 @@ struct TcCfg {
   static constexpr int NN1 = P + 1;
   static constexpr int NNL = DIM == 2 ? NN1 * NN1 : NN1 * NN1 * NN1;
   static constexpr int NL = NNL * NC;
-  static constexpr int KP = (NL + 7) / 8 * 8;      // K padded to the tf32 MMA step
+  static constexpr int KP = (NL + 15) / 16 * 16;   // K padded to the BF16 MMA step (16)
   static constexpr int NP = (NL + 15) / 16 * 16;   // N padded (M = 128 needs N % 16 == 0)
-  static constexpr int TMEM_COLS = NP <= 32 ? 32 : (NP <= 64 ? 64 : (NP <= 128 ? 128 : 256));
+  static constexpr int NACC = 4;                    // accumulators (levels 0..3)
+  static constexpr int TMEM_COLS = NACC * NP <= 32 ? 32 : (NACC * NP <= 64 ? 64 : (NACC * NP <= 128 ? 128 : (NACC * NP <= 256 ? 256 : 512)));
   static constexpr int TX = tc_tile_x(DIM, NL), TY = tc_tile_y(DIM, NL), TZ = tc_tile_z(DIM);
   static constexpr int EX = TX + 1, EY = TY + 1, EZ = DIM == 3 ? TZ + 1 : 1;
   static constexpr int NE = EX * EY * EZ;
   static constexpr int PX = EX * P + 1, PY = EY * P + 1, PZ = DIM == 3 ? EZ * P + 1 : 1;
   static constexpr int PATCH = PX * PY * PZ * NC;
   static constexpr int LBO = 128;                   // bytes between K-adjacent core matrices
-  static constexpr int SBO = (KP / 4) * 128;        // bytes between M/N-adjacent core matrices
-  static constexpr int A_FLOATS = 128 * KP;
-  static constexpr int B_FLOATS = NP * KP;
-  static constexpr size_t OFF_A_HI = 0;
-  static constexpr size_t OFF_A_LO = OFF_A_HI + 4 * (size_t)A_FLOATS;
-  static constexpr size_t OFF_B_HI = OFF_A_LO + 4 * (size_t)A_FLOATS;
-  static constexpr size_t OFF_B_LO = OFF_B_HI + 4 * (size_t)B_FLOATS;
-  static constexpr size_t OFF_PATCH = (OFF_B_LO + 4 * (size_t)B_FLOATS + 15) / 16 * 16;
-  static constexpr size_t OFF_OFF = OFF_PATCH + 8 * (size_t)PATCH;
-  static constexpr size_t OFF_XS = (OFF_OFF + 4 * (size_t)NL + 15) / 16 * 16;   // 8 warps x NL f32
-  static constexpr size_t OFF_BAR = (OFF_XS + 4 * (size_t)8 * NL + 15) / 16 * 16;
-  static constexpr size_t SMEM = OFF_BAR + 32;
+  static constexpr int SBO = (KP / 8) * 128;        // bytes between M/N-adjacent core matrices
+  static constexpr int A_SLICE = 128 * KP;          // BF16 elements of one A slice
+  static constexpr int B_SLICE = NP * KP;           // BF16 elements of one B slice
+  static constexpr size_t A_BYTES = 2 * 2 * (size_t)A_SLICE;  // two slots
+  static constexpr size_t B_BYTES = 4 * 2 * (size_t)B_SLICE;  // four digit slices
+  static constexpr size_t Y_BYTES = 8 * (size_t)NE * NL;      // (D0, L) per (cell, row)
+  static constexpr bool Y_ALIAS = Y_BYTES <= A_BYTES + B_BYTES;
+  static constexpr size_t OFF_A = 0;
+  static constexpr size_t OFF_B = OFF_A + A_BYTES;
+  static constexpr size_t OFF_Y = Y_ALIAS ? 0 : OFF_B + B_BYTES;
+  static constexpr size_t OFF_PATCH = ((Y_ALIAS ? OFF_B + B_BYTES : OFF_Y + Y_BYTES) + 15) / 16 * 16;
+  static constexpr size_t OFF_E = OFF_PATCH + 8 * (size_t)PATCH;           // int E[128]
+  static constexpr size_t OFF_F = OFF_E + 4 * 128;                           // int F[NP]
+  static constexpr size_t OFF_OFF = OFF_F + 4 * (size_t)NP;                  // int off[KP]
+  static constexpr size_t OFF_XS = (OFF_OFF + 4 * (size_t)KP + 15) / 16 * 16;  // 8 warps x 2 x NL floats
+  static constexpr size_t OFF_BAR = (OFF_XS + 4 * 2 * 8 * (size_t)NL + 15) / 16 * 16;
+  static constexpr size_t SMEM = OFF_BAR + 64;
+  // never co-schedule more CTAs on an SM than its 512 TMEM columns can hold
+  static constexpr int CTA_TMEM_MAX = 512 / TMEM_COLS;
+  static constexpr size_t SMEM_FLOOR = 233472 / (CTA_TMEM_MAX + 1) - 1024 + 16;
+  static constexpr size_t SMEM_LAUNCH = SMEM > SMEM_FLOOR ? SMEM : SMEM_FLOOR;
   static_assert(NE <= 128, "halo'd tile must fit one M = 128 MMA");
-  static_assert((size_t)NE * NL <= (size_t)A_FLOATS, "element buffer aliases A_hi");
+  static_assert(KP % 8 == 0 && (KP / 8) <= 32, "K layout");
 };
 
-// core-matrix offset (in floats) of element (row, k) of a K-major operand with KP columns
 template <int KP>
-__host__ __device__ __forceinline__ int core_offset(int row, int k) {
-  return (row >> 3) * (KP / 4) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+__host__ __device__ __forceinline__ int bf16_core_offset(int row, int k) {
+  return (row >> 3) * (KP / 8) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-template <int DIM, int P, int NC>
+// scheme: 0 exact, 1 bf16x3, 2 bf16
+template <int DIM, int P, int NC, int SCHEME>
 __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double* __restrict__ u,
-                                                    double* __restrict__ out, int mode, int passes) {
+                                                    double* __restrict__ out, int mode) {
   using C = TcCfg<DIM, P, NC>;
   constexpr int NL = C::NL, NN1 = C::NN1, KP = C::KP, NP = C::NP;
-  constexpr int EX = C::EX, EY = C::EY, PX = C::PX, PY = C::PY, PZ = C::PZ;
+  constexpr int EX = C::EX, EY = C::EY, PX = C::PX, PY = C::PY;
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* A_hi = reinterpret_cast<float*>(smem + C::OFF_A_HI);
-  float* A_lo = reinterpret_cast<float*>(smem + C::OFF_A_LO);
-  float* B_hi = reinterpret_cast<float*>(smem + C::OFF_B_HI);
-  float* B_lo = reinterpret_cast<float*>(smem + C::OFF_B_LO);
+  uint16_t* A = reinterpret_cast<uint16_t*>(smem + C::OFF_A);
+  uint16_t* B = reinterpret_cast<uint16_t*>(smem + C::OFF_B);
+  float* yD = reinterpret_cast<float*>(smem + C::OFF_Y);      // level-0 part
+  float* yL = yD + C::NE * NL;                                // levels 1-3 part
   double* patch = reinterpret_cast<double*>(smem + C::OFF_PATCH);
+  int* Eb = reinterpret_cast<int*>(smem + C::OFF_E);
+  int* Fr = reinterpret_cast<int*>(smem + C::OFF_F);
   int* off = reinterpret_cast<int*>(smem + C::OFF_OFF);
   float* xs = reinterpret_cast<float*>(smem + C::OFF_XS);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 8);
-  float* ybuf = A_hi;  // reused once the MMAs have completed
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // 0: B copy, 1: MMA phase 1, 2: phase 2
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x;
@@ -144,21 +214,33 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   const int X0 = bx * C::TX, Y0 = by * C::TY, Z0 = bz * C::TZ;
   const int X1 = min(X0 + C::TX, pb.n[0]), Y1 = min(Y0 + C::TY, pb.n[1]);
   const int Z1 = DIM == 3 ? min(Z0 + C::TZ, pb.n[2]) : 1;
-  const int ox0 = X0 * P, ox1 = X1 * P + (X1 == pb.n[0] ? 1 : 0);
-  const int oy0 = Y0 * P, oy1 = Y1 * P + (Y1 == pb.n[1] ? 1 : 0);
-  const int oz0 = DIM == 3 ? Z0 * P : 0;
-  const int oz1 = DIM == 3 ? Z1 * P + (Z1 == pb.n[2] ? 1 : 0) : 1;
   const int gx0 = (X0 - 1) * P, gy0 = (Y0 - 1) * P, gz0 = DIM == 3 ? (Z0 - 1) * P : 0;
 
-  // ---- set-up: TMEM, barrier, observers, operands
+  // ---- set-up: TMEM, barriers, K_ref digits (bulk copy), observers
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(C::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 32) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[b])));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("fence.proxy.async.shared::cta;");
+    // K_ref digit slices: one bulk-async copy global -> shared, completion on bars[0]
+    const uint32_t bytes = (uint32_t)C::B_BYTES;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(B)),
+                 "l"(pb.tc_bimg), "r"(bytes), "r"(smem_u32(&bars[0]))
+                 : "memory");
+  }
+  for (int i = tid; i < NP; i += blockDim.x) Fr[i] = pb.tc_frow ? pb.tc_frow[i] : 0;
+  for (int i = tid; i < 128; i += blockDim.x) Eb[i] = SCHEME == 0 ? 0 : kNoScale;
+  for (int j = tid; j < KP; j += blockDim.x) {
+    int node = j / NC, comp = j % NC;
+    int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
+    off[j] = j < NL ? ((c * PY + b) * PX + a) * NC + comp : -1;
   }
   unsigned long long k = 0;
   if (mode == kModeCDM) k = *((volatile unsigned long long*)pb.step);
@@ -170,21 +252,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
       pb.ring[(size_t)(k % (unsigned long long)pb.ring_cap) * pb.n_obs_rows + r] = acc;
     }
   }
-  {
-    const float4* bh = reinterpret_cast<const float4*>(pb.tc_bimg);
-    const float4* bl = reinterpret_cast<const float4*>(pb.tc_bimg + C::B_FLOATS);
-    float4* sh = reinterpret_cast<float4*>(B_hi);
-    float4* sl = reinterpret_cast<float4*>(B_lo);
-    for (int i = tid; i < C::B_FLOATS / 4; i += blockDim.x) {
-      sh[i] = bh[i];
-      sl[i] = bl[i];
-    }
-  }
-  for (int j = tid; j < NL; j += blockDim.x) {
-    int node = j / NC, comp = j % NC;
-    int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
-    off[j] = ((c * PY + b) * PX + a) * NC + comp;
-  }
+  // node patch of u^k (zero outside the lattice)
   for (int i = tid; i < C::PATCH; i += blockDim.x) {
     int comp = i % NC, node = i / NC;
     int px = node % PX, py = (node / PX) % PY, pz = node / (PX * PY);
@@ -196,113 +264,250 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   }
   __syncthreads();
 
-  // ---- gather X into the UMMA operand layout: a warp writes one 8 x 4 core matrix
-  for (int idx = tid; idx < C::A_FLOATS; idx += blockDim.x) {
-    int within = idx & 31, core = idx >> 5;
-    int rg = core / (KP / 4), kg = core - rg * (KP / 4);
-    int m = rg * 8 + (within >> 2), j = kg * 4 + (within & 3);
-    uint32_t v = 0u;
-    if (m < C::NE && j < NL) {
+  // ---- per-cell row exponent (largest biased FP64 exponent of the gathered vector)
+  if (SCHEME == 0) {
+    for (int idx = tid; idx < C::NE * NL; idx += blockDim.x) {
+      int m = idx / NL, j = idx - m * NL;
       int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-      const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
-      v = f64_to_f32_bits(xe[off[j]]);
+      double x = patch[((elz * P * PY + ely * P) * PX + elx * P) * NC + off[j]];
+      int eb = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+      if (eb > 0) atomicMax(&Eb[m], eb);
     }
-    uint32_t hi = v & 0xFFFFE000u;
-    A_hi[idx] = __uint_as_float(hi);
-    A_lo[idx] = __uint_as_float(v) - __uint_as_float(hi);
+    __syncthreads();
+  }
+
+  // ---- A digits: each work item writes one 8-element row of a core matrix (16 bytes)
+  // of slots 0 and 1; slices 2 and 3 of the exact scheme are kept in registers
+  constexpr int KG = KP / 8;
+  constexpr int ITEMS = 128 * KG;
+  constexpr int IPT = (ITEMS + 255) / 256;
+  uint32_t keep[IPT][8];  // packed BF16 pairs of slices 2, 3 (exact scheme)
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    int item = tid + it * 256;
+    if (item >= ITEMS) break;
+    int m = item / KG, kg = item - m * KG;
+    uint16_t d[4][8];
+    int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
+    const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int j = kg * 8 + q;
+      double x = (m < C::NE && j < NL) ? xe[off[j]] : 0.0;
+      if (SCHEME == 0) {
+        long long bits = __double_as_longlong(x);
+        int eb = (int)((bits >> 52) & 0x7ff);
+        long long V = 0;
+        if (eb > 0) {
+          int sh = 21 + (Eb[m] - eb);  // >= 21
+          unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          unsigned long long mag = sh < 64 ? ((M >> (sh - 1)) + 1ull) >> 1 : 0ull;  // round half up
+          V = bits < 0 ? -(long long)mag : (long long)mag;
+        }
+        long long d0 = (V + (1ll << 23)) >> 24;
+        long long r = V - (d0 << 24);
+        long long d1 = (r + (1ll << 15)) >> 16;
+        r -= d1 << 16;
+        long long d2 = (r + (1ll << 7)) >> 8;
+        long long d3 = r - (d2 << 8);
+        d[0][q] = bf16_of_small_int((int)d0);
+        d[1][q] = bf16_of_small_int((int)d1);
+        d[2][q] = bf16_of_small_int((int)d2);
+        d[3][q] = bf16_of_small_int((int)d3);
+      } else {
+        float xf = f64_to_f32_rn(x);
+        uint16_t h = bf16_rn(xf);
+        float hf = __uint_as_float((uint32_t)h << 16);
+        d[0][q] = h;
+        d[1][q] = bf16_rn(xf - hf);
+        d[2][q] = 0;
+        d[3][q] = 0;
+      }
+    }
+    int o = bf16_core_offset<KP>(m, kg * 8);
+    uint4 s0, s1;
+    s0.x = d[0][0] | ((uint32_t)d[0][1] << 16); s0.y = d[0][2] | ((uint32_t)d[0][3] << 16);
+    s0.z = d[0][4] | ((uint32_t)d[0][5] << 16); s0.w = d[0][6] | ((uint32_t)d[0][7] << 16);
+    s1.x = d[1][0] | ((uint32_t)d[1][1] << 16); s1.y = d[1][2] | ((uint32_t)d[1][3] << 16);
+    s1.z = d[1][4] | ((uint32_t)d[1][5] << 16); s1.w = d[1][6] | ((uint32_t)d[1][7] << 16);
+    *reinterpret_cast<uint4*>(A + o) = s0;
+    *reinterpret_cast<uint4*>(A + C::A_SLICE + o) = s1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      keep[it][q] = d[2][2 * q] | ((uint32_t)d[2][2 * q + 1] << 16);
+      keep[it][4 + q] = d[3][2 * q] | ((uint32_t)d[3][2 * q + 1] << 16);
+    }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  const uint32_t aS[2] = {smem_u32(A), smem_u32(A + C::A_SLICE)};
+  const uint32_t bS0 = smem_u32(B);
+  bool ok = true;
 
-  // ---- MMA issue (one thread): Y[128 x NP] = X[128 x KP] K_ref^T
+  // ---- phase 1 MMAs (A slots hold x-digit slices 0 and 1)
   if (tid == 0) {
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
-    const uint32_t a_op[3] = {smem_u32(A_hi), smem_u32(A_hi), smem_u32(A_lo)};
-    const uint32_t b_op[3] = {smem_u32(B_hi), smem_u32(B_lo), smem_u32(B_hi)};
-    int first = 1;
-    for (int ps = 0; ps < passes; ++ps) {
-      for (int kk = 0; kk < KP / 8; ++kk) {
-        uint64_t da = umma_desc(a_op[ps] + kk * 2 * C::LBO, C::LBO, C::SBO);
-        uint64_t db = umma_desc(b_op[ps] + kk * 2 * C::LBO, C::LBO, C::SBO);
-        uint32_t acc = first ? 0u : 1u;
-        first = 0;
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    ok = mbar_wait(smem_u32(&bars[0]), 0);  // K_ref digits have landed
+    if (ok) {
+      // (s, t, level, first-in-chain)
+      const int S1 = SCHEME == 0 ? 7 : (SCHEME == 1 ? 3 : 1);
+      const int ps[7] = {0, 0, 1, 0, 1, 0, 1};
+      const int pt[7] = {0, 1, 0, 2, 1, 3, 2};
+      const int pl[7] = {0, 1, 1, 2, 2, 3, 3};
+      const int pf[7] = {1, 1, 0, 1, 0, 1, 0};
+      // bf16x3: hi.hi, hi.lo (B slice 1 = K lo), lo.hi -> all into level 0
+      const int qs[3] = {0, 0, 1};
+      const int qt[3] = {0, 1, 0};
+      for (int w = 0; w < S1; ++w) {
+        int s = SCHEME == 0 ? ps[w] : qs[w], t = SCHEME == 0 ? pt[w] : qt[w];
+        int l = SCHEME == 0 ? pl[w] : 0;
+        int first = SCHEME == 0 ? pf[w] : (w == 0);
+        uint32_t acc_addr = tmem + (uint32_t)(l * NP);
+        for (int kk = 0; kk < KP / 16; ++kk) {
+          uint64_t da = umma_desc(aS[s] + kk * 2 * C::LBO, C::LBO, C::SBO);
+          uint64_t db = umma_desc(bS0 + (uint32_t)(t * C::B_SLICE * 2) + kk * 2 * C::LBO, C::LBO, C::SBO);
+          mma_bf16(acc_addr, da, db, idesc, (first && kk == 0) ? 0u : 1u);
+        }
       }
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        smem_u32(mbar)));
+    mma_commit(smem_u32(&bars[1]));
   }
-  // bounded wait for the MMAs (phase 0)
-  uint32_t ready = 0;
-  for (int it = 0; it < (1 << 24) && !ready; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ready)
-        : "r"(smem_u32(mbar)), "r"(0));
+  if (SCHEME == 0) {
+    // slices 2 and 3 overwrite the slots once phase 1 has consumed them
+    bool r1 = mbar_wait(smem_u32(&bars[1]), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      int item = tid + it * 256;
+      if (item >= ITEMS) break;
+      int m = item / KG, kg = item - m * KG;
+      int o = bf16_core_offset<KP>(m, kg * 8);
+      *reinterpret_cast<uint4*>(A + o) = make_uint4(keep[it][0], keep[it][1], keep[it][2], keep[it][3]);
+      *reinterpret_cast<uint4*>(A + C::A_SLICE + o) = make_uint4(keep[it][4], keep[it][5], keep[it][6], keep[it][7]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      if (ok && r1) {
+        // (2,0) -> level 2, (2,1) -> level 3, (3,0) -> level 3
+        const int qs2[3] = {0, 0, 1};
+        const int qt2[3] = {0, 1, 0};
+        const int ql2[3] = {2, 3, 3};
+        for (int w = 0; w < 3; ++w) {
+          uint32_t acc_addr = tmem + (uint32_t)(ql2[w] * NP);
+          for (int kk = 0; kk < KP / 16; ++kk) {
+            uint64_t da = umma_desc(aS[qs2[w]] + kk * 2 * C::LBO, C::LBO, C::SBO);
+            uint64_t db = umma_desc(bS0 + (uint32_t)(qt2[w] * C::B_SLICE * 2) + kk * 2 * C::LBO, C::LBO, C::SBO);
+            mma_bf16(acc_addr, da, db, idesc, 1u);
+          }
+        }
+      }
+      mma_commit(smem_u32(&bars[2]));
+    }
   }
+  const bool ready = mbar_wait(smem_u32(&bars[SCHEME == 0 ? 2 : 1]), 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!ready) {
-    if (tid == 0) atomicOr(pb.flags, 2);  // timeout: report, skip the result
+    if (tid == 0) atomicOr(pb.flags, 2);
   } else if (warp < 4) {
+    // ---- drain TMEM: level 0 -> yD (exact integers), levels 1-3 -> yL (FP32)
     const int m = warp * 32 + lane;
-#pragma unroll
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
     for (int c0 = 0; c0 < NP; c0 += 16) {
-      uint32_t r[16];
-      uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(addr));
+      uint32_t r[4][16];
+#pragma unroll
+      for (int l = 0; l < (SCHEME == 0 ? 4 : 1); ++l) {
+        uint32_t addr = lane_base + (uint32_t)(l * NP + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]), "=r"(r[l][5]),
+              "=r"(r[l][6]), "=r"(r[l][7]), "=r"(r[l][8]), "=r"(r[l][9]), "=r"(r[l][10]), "=r"(r[l][11]),
+              "=r"(r[l][12]), "=r"(r[l][13]), "=r"(r[l][14]), "=r"(r[l][15])
+            : "r"(addr));
+      }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (m < C::NE) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (c0 + j < NL) ybuf[m * NL + c0 + j] = __uint_as_float(r[j]);
+        for (int q = 0; q < 16; ++q) {
+          int i = c0 + q;
+          if (i < NL) {
+            yD[m * NL + i] = __uint_as_float(r[0][q]);
+            float lo = 0.f;
+            if (SCHEME == 0)
+              lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
+                        fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f, __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
+            yL[m * NL + i] = lo;
+          }
+        }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
 
-  // ---- cut and outside cells: replace their rows (one warp per cell)
+  // ---- cut and outside cells replace their rows (double-FP32 on the CUDA cores)
   for (int m = warp; m < C::NE; m += 8) {
     int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
     int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
     bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
-    if (!in_dom) continue;
-    int64_t cell = ((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex;
-    uint8_t cl = pb.cls[cell];
+    uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
     if (cl == 2) continue;
     if (cl == 0) {
-      for (int i = lane; i < NL; i += 32) ybuf[m * NL + i] = 0.f;
+      for (int i = lane; i < NL; i += 32) {
+        yD[m * NL + i] = 0.f;
+        yL[m * NL + i] = 0.f;
+      }
+      if (lane == 0) Eb[m] = kNoScale;
       continue;
     }
     const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
-    float* xw = xs + warp * NL;
-    for (int j = lane; j < NL; j += 32) xw[j] = __uint_as_float(f64_to_f32_bits(xe[off[j]]));
-    __syncwarp();
-    const float* K = pb.Kcut32 + (size_t)pb.cut_index[cell] * NL * NL;
-    for (int i = lane; i < NL; i += 32) {
-      float acc = 0.f;
-#pragma unroll 4
-      for (int j = 0; j < NL; ++j) acc = fmaf(K[(size_t)j * NL + i], xw[j], acc);
-      ybuf[m * NL + i] = acc;
+    float* xh = xs + warp * 2 * NL;
+    float* xl = xh + NL;
+    for (int j = lane; j < NL; j += 32) {
+      double x = xe[off[j]];
+      float h = f64_to_f32_rn(x);
+      xh[j] = h;
+      xl[j] = f64_to_f32_rn(x - f32_to_f64_scaled(h, 0));
     }
     __syncwarp();
+    const int64_t cell = ((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex;
+    const float* Kh = pb.Kcut32 + (size_t)pb.cut_index[cell] * 2 * NL * NL;
+    const float* Kl = Kh + NL * NL;
+    for (int i = lane; i < NL; i += 32) {
+      float s = 0.f, c = 0.f;
+      for (int j = 0; j < NL; ++j) {
+        float kh = Kh[(size_t)j * NL + i], kl = Kl[(size_t)j * NL + i];
+        float p = kh * xh[j];
+        float pe = fmaf(kh, xh[j], -p);          // exact error of the product
+        pe = fmaf(kh, xl[j], fmaf(kl, xh[j], pe));
+        float t, e;
+        two_sum(s, p, t, e);
+        s = t;
+        c += e + pe;
+      }
+      float hs, he;
+      two_sum(s, c, hs, he);
+      yD[m * NL + i] = hs;
+      yL[m * NL + i] = he;
+    }
+    __syncwarp();
+    if (lane == 0) Eb[m] = kNoScale;
   }
   __syncthreads();
 
-  // ---- node-centric assembly and the FP64 update
-  const int nox = ox1 - ox0, noy = oy1 - oy0, noz = oz1 - oz0;
-  const int n_own = nox * noy * noz * NC;
+  // ---- node-centric assembly and the FP64 update (owned nodes, no runtime division)
+  const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
+  const int nox = (X1 - X0) * P + (X1 == pb.n[0] ? 1 : 0);
+  const int noy = (Y1 - Y0) * P + (Y1 == pb.n[1] ? 1 : 0);
+  const int noz = DIM == 3 ? (Z1 - Z0) * P + (Z1 == pb.n[2] ? 1 : 0) : 1;
+  constexpr int WX = C::TX * P + 1, WY = C::TY * P + 1, WZ = DIM == 3 ? C::TZ * P + 1 : 1;
   double fk = 0.0;
   int src_lo = 0, src_hi = 0;
   if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) {
@@ -311,44 +516,50 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     if (src_hi > src_lo) fk = ricker_tc((double)k * pb.dt, pb.f_e);
   }
   bool bad = false;
-  for (int i = tid; i < n_own; i += blockDim.x) {
-    int comp = i % NC, node = i / NC;
-    int gx = ox0 + node % nox, gy = oy0 + (node / nox) % noy, gz = oz0 + node / (nox * noy);
-    int qx = gx / P, qy = gy / P, qz = gz / P;
-    int exs[2], eys[2], ezs[2], nxe = 0, nye = 0, nze = 0;
-    if (DIM == 3) {
-      if (gz % P == 0 && qz - 1 >= 0) ezs[nze++] = qz - 1;
-      if (qz < pb.n[2]) ezs[nze++] = qz;
-    } else {
-      ezs[nze++] = 0;
-    }
-    if (gy % P == 0 && qy - 1 >= 0) eys[nye++] = qy - 1;
-    if (qy < pb.n[1]) eys[nye++] = qy;
-    if (gx % P == 0 && qx - 1 >= 0) exs[nxe++] = qx - 1;
-    if (qx < pb.n[0]) exs[nxe++] = qx;
-    float ku = 0.f;
+  constexpr int TOTAL = WX * WY * WZ * NC;
+  for (int i = tid; i < TOTAL; i += blockDim.x) {
+    const int comp = i % NC, node = i / NC;
+    const int lx = node % WX, ly = (node / WX) % WY, lz = node / (WX * WY);
+    if (lx >= nox || ly >= noy || lz >= noz) continue;
+    const int gx = ox0 + lx, gy = oy0 + ly, gz = oz0 + lz;
+    // patch-local coordinates: node index relative to the halo'd tile origin
+    const int px = lx + P, py = ly + P, pz = DIM == 3 ? lz + P : 0;
+    const int cx = px / P, cy = py / P, cz = DIM == 3 ? pz / P : 0;
+    const int nxe = (px % P == 0) ? 2 : 1, nye = (py % P == 0) ? 2 : 1;
+    const int nze = DIM == 3 ? ((pz % P == 0) ? 2 : 1) : 1;
+    double hi = 0.0;
+    float lo = 0.f;
+    bool first = true;
     for (int iz = 0; iz < nze; ++iz)
       for (int iy = 0; iy < nye; ++iy)
         for (int ix = 0; ix < nxe; ++ix) {
-          int ex = exs[ix], ey = eys[iy], ez = ezs[iz];
-          int el = ((DIM == 3 ? ez - (Z0 - 1) : 0) * EY + (ey - (Y0 - 1))) * EX + (ex - (X0 - 1));
-          int lr = ((DIM == 3 ? (gz - ez * P) * NN1 : 0) + (gy - ey * P)) * NN1 + (gx - ex * P);
-          ku += ybuf[el * NL + lr * NC + comp];
+          const int ecx = cx - (nxe - 1) + ix, ecy = cy - (nye - 1) + iy, ecz = DIM == 3 ? cz - (nze - 1) + iz : 0;
+          if (ecx >= EX || ecy >= EY || (DIM == 3 && ecz >= C::EZ)) continue;
+          const int m = (ecz * EY + ecy) * EX + ecx;
+          const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
+          const int e = Eb[m];
+          const int sh = (e == kNoScale) ? 0 : e - 1023 + Fr[row] - 14;
+          double v = f32_to_f64_scaled(yD[m * NL + row], sh);
+          hi = first ? v : hi + v;
+          first = false;
+          lo += f32_scale(yL[m * NL + row], sh);
         }
-    int64_t dof = (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp;
+    const int64_t dof = (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp;
     if (mode == kModeApply) {
-      out[dof] = f32_to_f64_bits(ku);
+      out[dof] = hi + f32_to_f64_scaled(lo, 0);
       continue;
     }
-    float m32 = pb.minv32[dof];
-    if (!(m32 > 0.f)) continue;
-    float f = 0.f;
+    const float mh = pb.minv32[dof];
+    if (!(mh > 0.f)) continue;
+    const float ml = pb.minv32[pb.n_lat_dof + dof];
+    double t = -hi;
     for (int s2 = src_lo; s2 < src_hi; ++s2)
-      if (pb.tsrc_dof[s2] == dof) f += (float)(pb.tsrc_val[s2] * fk);
-    float d32 = m32 * (f - ku);
+      if (pb.tsrc_dof[s2] == dof) t += pb.tsrc_val[s2] * fk;
+    const float r = f64_to_f32_rn(t) - lo;
+    const float d32 = fmaf(mh, r, ml * r);
     if (!isfinite(d32)) bad = true;
-    double delta = f32_to_f64_bits(d32);
-    double uval = patch[(((gz - gz0) * PY + (gy - gy0)) * PX + (gx - gx0)) * NC + comp];
+    const double delta = f32_to_f64_scaled(d32, 0);
+    const double uval = patch[(((gz - gz0) * PY + (gy - gy0)) * PX + (gx - gx0)) * NC + comp];
     if (mode == kModeCDM)
       out[dof] = fma(2.0, uval, -out[dof]) + delta;
     else
@@ -393,34 +604,37 @@ void op_tc_tiles(int dim, int p, int ncomp, int* t) {
 void op_tc_dims(int dim, int p, int ncomp, int* kp, int* np) {
   int nl = ncomp;
   for (int k = 0; k < dim; ++k) nl *= p + 1;
-  *kp = (nl + 7) / 8 * 8;
+  *kp = (nl + 15) / 16 * 16;
   *np = (nl + 15) / 16 * 16;
 }
 
 int op_tc_core_offset(int kp, int row, int k) {
-  return (row >> 3) * (kp / 4) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+  return (row >> 3) * (kp / 8) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-template <int D, int P, int N>
-static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* out, int mode, int passes,
-                               cudaStream_t st) {
+template <int D, int P, int N, int S>
+static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* out, int mode, cudaStream_t st) {
   using C = TcCfg<D, P, N>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(op_tc_kernel<D, P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(op_tc_kernel<D, P, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_LAUNCH);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   int blocks = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
-  op_tc_kernel<D, P, N><<<blocks, 256, C::SMEM, st>>>(pb, u, out, mode, passes);
+  op_tc_kernel<D, P, N, S><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode);
   return cudaGetLastError();
 }
 
-cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int passes,
+cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme,
                          cudaStream_t st) {
-#define X(D, P, N) \
-  if (pb.dim == D && pb.p == P && pb.ncomp == N) return launch_tc_t<D, P, N>(pb, u, out, mode, passes, st);
+#define X(D, P, N)                                                               \
+  if (pb.dim == D && pb.p == P && pb.ncomp == N) {                               \
+    if (scheme == 0) return launch_tc_t<D, P, N, 0>(pb, u, out, mode, st);       \
+    if (scheme == 1) return launch_tc_t<D, P, N, 1>(pb, u, out, mode, st);       \
+    return launch_tc_t<D, P, N, 2>(pb, u, out, mode, st);                        \
+  }
   IBFEM_TC_SHAPES(X)
 #undef X
   return cudaErrorInvalidValue;

@@ -157,30 +157,73 @@ void Handle::build_device() {
   n_blocks = op_fp64_blocks(pb);
   partials = static_cast<double*>(dalloc(2 * (size_t)n_blocks * sizeof(double)));
   if (opt.precision != IBFEM_FP64) {
-    // K_ref as the UMMA B operand (row i = K_ref[i, :], K-major core matrices), TF32 hi/lo
+    // K_ref as the UMMA B operand (row i = K_ref[i, :], K-major BF16 core matrices), four
+    // slices: balanced 8-bit digits (exact scheme) or BF16 hi / lo splits
     int kp = 0, np = 0;
     op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
-    std::vector<float> img(2 * (size_t)np * kp, 0.f);
-    for (int i = 0; i < np; ++i)
-      for (int j = 0; j < kp; ++j) {
-        double v = (i < s.n_loc && j < s.n_loc) ? s.Kref[(size_t)i * s.n_loc + j] : 0.0;
-        float f = (float)v;
-        uint32_t b;
-        std::memcpy(&b, &f, 4);
-        b &= 0xFFFFE000u;
-        float hi;
-        std::memcpy(&hi, &b, 4);
-        float lo = (float)(v - (double)hi);
+    const size_t slice = (size_t)np * kp;
+    std::vector<uint16_t> img(4 * slice, 0);
+    std::vector<int> frow(np, 0);
+    auto bf16 = [](float f) {
+      uint32_t b;
+      std::memcpy(&b, &f, 4);
+      b += 0x7fffu + ((b >> 16) & 1u);
+      return (uint16_t)(b >> 16);
+    };
+    auto bf16_to_f = [](uint16_t h) {
+      uint32_t b = (uint32_t)h << 16;
+      float f;
+      std::memcpy(&f, &b, 4);
+      return f;
+    };
+    for (int i = 0; i < s.n_loc; ++i) {
+      double amax = 0.0;
+      for (int j = 0; j < s.n_loc; ++j) amax = std::max(amax, std::fabs(s.Kref[(size_t)i * s.n_loc + j]));
+      int F = 0;
+      if (amax > 0.0) F = (int)std::floor(std::log2(amax));
+      if (amax > 0.0 && std::ldexp(1.0, F + 1) <= amax) ++F;   // guard log2 rounding
+      if (amax > 0.0 && std::ldexp(1.0, F) > amax) --F;
+      frow[i] = F;
+      for (int j = 0; j < s.n_loc; ++j) {
+        double v = s.Kref[(size_t)i * s.n_loc + j];
         int o = op_tc_core_offset(kp, i, j);
-        img[o] = hi;
-        img[(size_t)np * kp + o] = lo;
+        if (tc_scheme() == 0) {
+          long long W = std::llround(std::ldexp(v, 31 - F));
+          long long c0 = (W + (1ll << 23)) >> 24;
+          long long r = W - (c0 << 24);
+          long long c1 = (r + (1ll << 15)) >> 16;
+          r -= c1 << 16;
+          long long c2 = (r + (1ll << 7)) >> 8;
+          long long c3 = r - (c2 << 8);
+          long long c[4] = {c0, c1, c2, c3};
+          for (int t = 0; t < 4; ++t) img[t * slice + o] = bf16((float)c[t]);
+        } else {
+          uint16_t h = bf16((float)v);
+          img[o] = h;
+          if (tc_scheme() == 1) img[slice + o] = bf16((float)(v - (double)bf16_to_f(h)));
+        }
       }
+    }
     pb.tc_bimg = upload(img);
-    std::vector<float> k32(s.Kcut.begin(), s.Kcut.end());
+    pb.tc_frow = upload(frow);
+    std::vector<float> k32(2 * (size_t)s.n_cut * s.n_loc * s.n_loc);
+    const size_t nl2 = (size_t)s.n_loc * s.n_loc;
+    for (int64_t c = 0; c < s.n_cut; ++c)
+      for (size_t q = 0; q < nl2; ++q) {
+        double v = s.Kcut[c * nl2 + q];
+        float h = (float)v;
+        k32[(2 * c) * nl2 + q] = h;
+        k32[(2 * c + 1) * nl2 + q] = (float)(v - (double)h);
+      }
     pb.Kcut32 = upload(k32);
-    std::vector<float> m32(s.n_lat_dof, 0.f);
+    std::vector<float> m32(2 * (size_t)s.n_lat_dof, 0.f);
     for (int64_t i = 0; i < s.n_lat_dof; ++i)
-      if (s.ML[i] > 0) m32[i] = (float)(1.0 / s.ML[i]);
+      if (s.ML[i] > 0) {
+        double v = 1.0 / s.ML[i];
+        float h = (float)v;
+        m32[i] = h;
+        m32[s.n_lat_dof + i] = (float)(v - (double)h);
+      }
     d_minv32 = upload(m32);
     pb.minv32 = d_minv32;
     op_tc_tiles(s.dim, s.p, s.ncomp, tc_tile);
@@ -275,10 +318,10 @@ void Handle::timed_collect() {
 // One CDM step with u = U[cur], out = U[1 - cur] (in place over u^{k-1}).
 void Handle::enqueue_step(int cur) {
   if (opt.precision != IBFEM_FP64) {
-    slot_name[1] = opt.precision == IBFEM_TF32X3_TC ? "op_tc_tf32x3_fused_cdm" : "op_tc_tf32_fused_cdm";
+    slot_name[1] = tc_scheme() == 0 ? "op_tc_exact_fused_cdm" : (tc_scheme() == 1 ? "op_tc_bf16x3_fused_cdm" : "op_tc_bf16_fused_cdm");
     if (timing) step_first_ev.push_back(ev_used);
     timed_begin(1);
-    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_passes(), stream), "op_tc");
+    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_scheme(), stream), "op_tc");
     timed_end();
     if (timing) step_last_ev.push_back(ev_used - 1);
     return;
@@ -407,7 +450,8 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   if (o.scheme == IBFEM_IMEX && o.precision != IBFEM_FP64)
     throw std::invalid_argument("IMEX runs in FP64 (precision must be IBFEM_FP64)");
   in.need_consistent_mass = o.scheme == IBFEM_IMEX;
-  if (o.precision != IBFEM_FP64 && o.precision != IBFEM_TF32X3_TC && o.precision != IBFEM_TF32_TC)
+  if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
+      o.precision != IBFEM_BF16_TC)
     throw std::invalid_argument("precision not supported by this build");
   if (o.precision != IBFEM_FP64 && !o.host_only &&
       !op_tc_supported(grid->dim, p, o.physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1))
@@ -698,7 +742,14 @@ int ibfem_set_dt(ibfem_t* h, double dt) {
   check(cudaMemcpyAsync(h->d_minv, minv.data(), minv.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "minv");
   std::vector<float> m32;
   if (h->d_minv32) {
-    m32.assign(minv.begin(), minv.end());
+    // two FP32 slices: hi then lo (the pair carries dt^2/m to about 48 bits)
+    m32.assign(2 * minv.size(), 0.f);
+    for (size_t i = 0; i < minv.size(); ++i) {
+      if (!(minv[i] > 0)) continue;
+      float hh = (float)minv[i];
+      m32[i] = hh;
+      m32[minv.size() + i] = (float)(minv[i] - (double)hh);
+    }
     check(cudaMemcpyAsync(h->d_minv32, m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream), "minv32");
   }
   check(cudaStreamSynchronize(h->stream), "set_dt");
@@ -907,7 +958,7 @@ int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
   check(cudaMemcpyAsync(h->W, lx.data(), lx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "x");
   OpInput in{h->W, nullptr, nullptr};
   if (h->opt.precision != IBFEM_FP64) {
-    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_passes(), h->stream), "apply_tc");
+    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_scheme(), h->stream), "apply_tc");
   } else {
     check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
     check(launch_op_fp64(h->dev, in, h->scratch, kModeApply, nullptr, h->stream), "apply");

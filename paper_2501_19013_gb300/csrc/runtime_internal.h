@@ -30,7 +30,8 @@ struct Handle {
   double* d_minv = nullptr;
   float* d_minv32 = nullptr;
   int tc_tile[3] = {1, 1, 1};
-  int tc_passes() const { return opt.precision == IBFEM_TF32X3_TC ? 3 : 1; }
+  // tensor-core scheme: 0 exact digit slices, 1 bf16 three-pass, 2 bf16 one pass
+  int tc_scheme() const { return opt.precision == IBFEM_EXACT_TC ? 0 : (opt.precision == IBFEM_BF16X3_TC ? 1 : 2); }
   // IMEX (Algorithm 2): host partition/factor and their device copies
   bool imex = false;
   ImexData imex_host;

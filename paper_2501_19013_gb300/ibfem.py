@@ -20,10 +20,10 @@ GEOM_NONE, GEOM_HOLES, GEOM_VOXELS, GEOM_ROTATED_BOX = 0, 1, 2, 3
 STAB_NONE, STAB_EVS, STAB_MASS_SCALING = 0, 1, 2
 SCALAR, ELASTIC_PLANE_STRAIN = 0, 1
 CDM, IMEX = 0, 1
-FP64, TF32X3_TC, TF32_TC, BF16_TC = 0, 1, 2, 3
+FP64, EXACT_TC, BF16X3_TC, BF16_TC = 0, 1, 2, 3
 SRC_NONE, SRC_POINT, SRC_EDGE_TRACTION = 0, 1, 2
 
-PRECISIONS = {"fp64": FP64, "tf32x3": TF32X3_TC, "tf32": TF32_TC, "bf16": BF16_TC}
+PRECISIONS = {"fp64": FP64, "exact": EXACT_TC, "bf16x3": BF16X3_TC, "bf16": BF16_TC}
 
 
 class IbfemError(RuntimeError):

@@ -1,9 +1,13 @@
-"""Mixed-precision tensor-core path (tcgen05, TF32 operands, FP64 state) against the oracle.
+"""Mixed-precision tensor-core path (tcgen05, FP64 state) against the FP64 oracle.
 
-The element contractions run in TF32 on the tensor cores (three passes hi*hi + hi*lo +
-lo*hi for about FP32 accuracy, or one pass); the state and the central-difference update
-stay FP64.  The bar for a mixed variant to count is a relative L2 error <= 1e-4 against the
-FP64 oracle after the configured steps.
+Schemes of the element contraction on the tensor cores:
+  exact  -- balanced 8-bit digit slices of u and K_ref in BF16, ten MMA chains accumulated
+            exactly per level, level 0 assembled in FP64 (about 32 significant bits);
+  bf16x3 -- BF16 hi/lo splits, three passes, FP32 accumulation;
+  bf16   -- one BF16 pass, FP32 accumulation.
+The state and the central-difference update stay FP64.  A mixed variant counts for the
+time-to-accuracy metric when its relative L2 error against the FP64 oracle after the
+configured steps is <= 1e-4.
 """
 import numpy as np
 import pytest
@@ -15,11 +19,11 @@ pytestmark = pytest.mark.gpu
 MIXED_BAR = 1e-4
 TC_CASES = ["plate_one_hole", "elastic_evs", "elastic_evs_ragged", "scalar_mass_scaling",
             "voxel_3d_evs", "voxel_3d_p2_ragged"]
-# relative error of one operator application K x for a random x
-APPLY_TOL = {"tf32x3": 2e-6, "tf32": 5e-3}
+# relative error of one application K x for a random x
+APPLY_TOL = {"exact": 1e-8, "bf16x3": 1e-4, "bf16": 2e-2}
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", ["exact", "bf16x3", "bf16"])
 @pytest.mark.parametrize("case", TC_CASES)
 def test_tc_apply_operator(case, prec):
     w = SMALL_CASES[case]()
@@ -32,28 +36,33 @@ def test_tc_apply_operator(case, prec):
 
 
 @pytest.mark.parametrize("case", TC_CASES)
-def test_tc_cdm_run_within_mixed_bar(case):
+def test_exact_scheme_cdm_run_within_mixed_bar(case):
     w = SMALL_CASES[case]()
     d = oracle_disc(w)
     dt = oracle_dt(d)
     u_o, up_o, s_o = oracle_cdm(w, d, dt, w.steps)
-    u_g, up_g, s_g = gpu_cdm(w, dt, w.steps, precision="tf32x3")
+    u_g, up_g, s_g = gpu_cdm(w, dt, w.steps, precision="exact")
     assert rel_l2(u_g, u_o) <= MIXED_BAR
     # observer series: error relative to the field amplitude (an observer the wave has not
     # reached sees only an exponentially small precursor, whose relative error is noise)
     assert np.abs(s_g - s_o).max() <= MIXED_BAR * np.abs(u_o).max()
 
 
-def test_tc_step_counter_and_ring_follow_the_fp64_path():
-    """Same step bookkeeping as the FP64 path: rows of the observer ring, resume."""
-    w = SMALL_CASES["plate_one_hole"]()
+def test_exact_scheme_is_deterministic_and_keeps_the_step_bookkeeping():
+    w = SMALL_CASES["elastic_evs_ragged"]()
     d = oracle_disc(w)
     dt = oracle_dt(d)
-    a = gpu_solver(w, precision="tf32x3")
-    a.set_dt(dt)
-    a.set_initial()
-    a.step(77)
-    rows = a.sample(1000)
-    assert rows.shape[0] == 78
-    assert a.info().step == 77
-    a.close()
+    u1, up1, s1 = gpu_cdm(w, dt, 77, precision="exact")
+    u2, up2, s2 = gpu_cdm(w, dt, 77, precision="exact")
+    assert np.array_equal(u1, u2) and np.array_equal(s1, s2)
+    assert s1.shape[0] == 78
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_fp32_accumulating_schemes_run(prec):
+    """The FP32-accumulating schemes run and stay finite; their error is reported, not gated."""
+    w = SMALL_CASES["elastic_evs"]()
+    d = oracle_disc(w)
+    dt = oracle_dt(d)
+    u_g, _, _ = gpu_cdm(w, dt, w.steps, precision=prec)
+    assert np.isfinite(u_g).all()
