@@ -99,10 +99,17 @@ class Clocks:
 
 
 GRID = 256
+WORKLOAD = "plate_holes_elastic"
 
 
 def workload_for_bench():
     from paper_2501_19013_gb300 import workloads as W
+    if WORKLOAD == "plate_holes_imex":
+        return W.plate_holes_imex(n=GRID if GRID != 256 else 512)
+    if WORKLOAD == "porous_voxel":
+        return W.porous_voxel(n=GRID if GRID != 256 else 64)
+    if WORKLOAD == "plate_one_hole":
+        return W.plate_one_hole()
     return W.plate_holes_elastic(n=GRID)
 
 
@@ -145,6 +152,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def parse_variant(v, w):
+    """'fp64' | 'exact' | 'bf16x3' | 'bf16' -> CDM with the workload's stabilisation;
+    'imex' -> Newmark IMEX (FP64); 'ms:<precision>' -> CDM with mass scaling."""
+    if v == "imex":
+        return w.with_(scheme="imex", stab="none"), "fp64"
+    if v.startswith("ms:"):
+        return w.with_(scheme="cdm", stab="mass_scaling"), v[3:]
+    return w.with_(scheme="cdm" if w.scheme != "imex" else "cdm",
+                   stab=w.stab if w.scheme != "imex" else "mass_scaling"), v
+
+
 def build_solver(w, precision, stream):
     from paper_2501_19013_gb300 import ibfem as ib
     s = ib.from_workload(w, precision=precision, stream=stream, torch_alloc=True)
@@ -152,6 +170,22 @@ def build_solver(w, precision, stream):
     s.set_source(kind, params, w.f0)
     s.set_observers(w.observers, capacity=w.steps + 1)
     return s
+
+
+def aggregate_replicas(step_ms, n_dof, world, device=None):
+    """Replicas: every rank advances its own copy of the workload.  The job's step time is
+    the slowest rank's; the job's throughput counts the DOFs of all ranks."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([step_ms, float(n_dof)], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        return float(mx[0].item()), float(sm[1].item()) / (float(mx[0].item()) * 1e-3)
+    return step_ms, n_dof / (step_ms * 1e-3)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -170,16 +204,19 @@ def run_ours(args, rank, world, local_rank):
     variants = [v for v in args.precisions.split(",") if v]
     results = {}
     ref_state = None
-    dt = None
+    dts = {}
     for prec in variants:
-        s = build_solver(w, prec, sptr)
+        wv, pv = parse_variant(prec, w)
+        s = build_solver(wv, pv, sptr)
         info = s.info()
-        if dt is None:
+        key = (wv.scheme, wv.stab)
+        if key not in dts:
             if args.dt > 0:
-                dt = args.dt
+                dts[key] = args.dt
             else:
                 dt_crit, lam, it = s.crit_dt(max_iter=2000, rtol=1e-7)
-                dt = w.dt_factor * dt_crit
+                dts[key] = w.dt_factor * dt_crit
+        dt = dts[key]
         s.set_dt(dt)
         s.set_initial()
         s.step_timed(args.warmup, flush.data_ptr(), FLUSH_BYTES)
@@ -204,6 +241,8 @@ def run_ours(args, rank, world, local_rank):
         steady_ms = e0.elapsed_time(e1) / args.steps
         # accuracy over the configured run (from rest, with the load)
         run_steps = w.steps if args.run_steps < 0 else args.run_steps
+        if args.run_time > 0:
+            run_steps = int(np.ceil(args.run_time / dt))
         s.set_initial()
         t0 = time.perf_counter()
         s.step(run_steps)
@@ -211,11 +250,12 @@ def run_ours(args, rank, world, local_rank):
         run_s = time.perf_counter() - t0
         u_end, _ = s.get_state()
         results[prec] = dict(step_ms=step_ms, kernels=kernels, steady_ms=steady_ms, info=info,
-                             clocks=clk, run_s=run_s, u_end=u_end, solver=s, wall=t_wall)
+                             clocks=clk, run_s=run_s, u_end=u_end, solver=s, wall=t_wall, dt=dt,
+                             run_steps=run_steps, scheme=wv.scheme, stab=wv.stab)
         if prec == "fp64":
             ref_state = u_end
     for prec, r in results.items():
-        if ref_state is not None:
+        if ref_state is not None and r["scheme"] == "cdm" and r["stab"] == results["fp64"]["stab"]:
             nr = np.linalg.norm(ref_state)
             r["rel_l2"] = float(np.linalg.norm(r["u_end"] - ref_state) / nr) if nr > 0 else 0.0
         else:
@@ -226,11 +266,7 @@ def run_ours(args, rank, world, local_rank):
     rb = results[best]
     n_dof = rb["info"].n_dof
     step_ms = rb["step_ms"]
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * n_dof / (step_ms * 1e-3)
+    step_ms, value = aggregate_replicas(step_ms, n_dof, world, dev if world > 1 else None)
 
     # roofline of the dominant kernel
     kname, kms = max(rb["kernels"].items(), key=lambda kv: kv[1])
@@ -283,8 +319,9 @@ def run_ours(args, rank, world, local_rank):
         variants_out[p] = {"dof_steps_per_s": r["info"].n_dof / (r["step_ms"] * 1e-3),
                            "ms_per_step": r["step_ms"], "steady_state_ms_per_step": r["steady_ms"],
                            "rel_l2_vs_fp64_after_run": r["rel_l2"],
-                           "run_steps": w.steps if args.run_steps < 0 else args.run_steps,
-                           "time_to_accuracy_s": (r["step_ms"] * 1e-3 * w.steps) if (r["rel_l2"] is not None and r["rel_l2"] <= 1e-4) else None,
+                           "run_steps": r["run_steps"], "dt": r["dt"], "scheme": r["scheme"],
+                           "stab": r["stab"], "run_wall_s": r["run_s"],
+                           "time_to_accuracy_s": (r["step_ms"] * 1e-3 * r["run_steps"]) if (r["rel_l2"] is not None and r["rel_l2"] <= 1e-4) else None,
                            "kernels_ms": r["kernels"]}
     launches = args.steps * len(rb["kernels"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -316,9 +353,13 @@ def main():
     ap.add_argument("--grid", type=int, default=256, help="cells per axis of the plate (profiling)")
     ap.add_argument("--dt", type=float, default=0.0, help="fixed dt instead of 0.9 dt_crit (profiling)")
     ap.add_argument("--run-steps", type=int, default=-1, help="steps of the accuracy run (-1: the workload's)")
+    ap.add_argument("--run-time", type=float, default=0.0, help="simulated time of the accuracy run (overrides steps)")
+    ap.add_argument("--workload", default="plate_holes_elastic",
+                    choices=["plate_holes_elastic", "plate_holes_imex", "porous_voxel", "plate_one_hole"])
     args = ap.parse_args()
-    global GRID
+    global GRID, WORKLOAD
     GRID = args.grid
+    WORKLOAD = args.workload
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

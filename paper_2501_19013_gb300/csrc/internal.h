@@ -40,6 +40,7 @@ struct DevProblem {
   // counters
   unsigned long long* step; // device step counter
   unsigned int* done;       // block-completion counter for the step increment
+  int* tile_counter;        // persistent tensor-core kernel: next tile to take (reset by the last block)
   int* flags;               // bit 0: non-finite state
   int tiles[3];             // tile grid of the fused kernel
   // mixed-precision tensor-core path

@@ -25,6 +25,7 @@
 // and u^{k+1} = (2 u^k - u^{k-1}) + delta in FP64: two FP64 operations per DOF plus one per
 // extra cell sharing the node, the only FP64 arithmetic of the step.
 // The K_ref digit image is copied into shared memory with the bulk-async (TMA) engine.
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -135,6 +136,52 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 constexpr int kNoScale = -100000;  // E_m marker: rows whose (D0, L) are already scaled
 
+// Asynchronous copy global -> shared of 8 or 16 bytes; src_bytes = 0 writes zeros.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// Balanced 8-bit digits of round(|x| 2^(31 - E)) for an FP64 x whose biased exponent is at
+// most em (the row's largest), sign applied to every digit; 32-bit integer operations only.
+// d0 in [0, 256], d1..d3 in [-128, 128) before the sign.
+__device__ __forceinline__ void fp64_digits(double x, int em, int d[4]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hw = (uint32_t)(bits >> 32), lw = (uint32_t)bits;
+  const int eb = (int)((hw >> 20) & 0x7ffu);
+  uint32_t V = 0;
+  if (eb > 0) {
+    const int sh = 21 + (em - eb);                 // >= 21
+    const uint32_t mh = (hw & 0xFFFFFu) | 0x100000u;  // top 21 bits of the 53-bit significand
+    if (sh < 32) {
+      uint32_t t = __funnelshift_r(lw, mh, sh);     // (mh:lw) >> sh, fits 32 bits for sh >= 21
+      uint32_t rb = (lw >> (sh - 1)) & 1u;          // rounding bit (sh - 1 < 32)
+      V = t + rb;
+      if (V < t) V = 0xFFFFFFFFu;                   // saturate the single all-ones carry case
+    } else if (sh < 53) {
+      uint32_t t = mh >> (sh - 32);
+      uint32_t rb = sh == 32 ? (lw >> 31) : ((mh >> (sh - 33)) & 1u);
+      V = t + rb;
+    }
+  }
+  const int d0 = (int)((V >> 24) + ((V >> 23) & 1u));
+  int r = (int)(V - ((uint32_t)d0 << 24));          // in [-2^23, 2^23)
+  const int d1 = (r + 0x8000) >> 16;
+  r -= d1 << 16;
+  const int d2 = (r + 0x80) >> 8;
+  const int d3 = r - (d2 << 8);
+  const bool neg = (hw >> 31) != 0;
+  d[0] = neg ? -d0 : d0;
+  d[1] = neg ? -d1 : d1;
+  d[2] = neg ? -d2 : d2;
+  d[3] = neg ? -d3 : d3;
+}
+
 }  // namespace
 
 __host__ __device__ constexpr int tc_tile_x(int dim, int nl) { return dim == 3 ? 4 : (nl >= 32 ? 8 : 15); }
@@ -162,7 +209,7 @@ struct TcCfg {
   static constexpr size_t A_BYTES = 2 * 2 * (size_t)A_SLICE;  // two slots
   static constexpr size_t B_BYTES = 4 * 2 * (size_t)B_SLICE;  // four digit slices
   static constexpr size_t Y_BYTES = 8 * (size_t)NE * NL;      // (D0, L) per (cell, row)
-  static constexpr bool Y_ALIAS = Y_BYTES <= A_BYTES + B_BYTES;
+  static constexpr bool Y_ALIAS = Y_BYTES <= A_BYTES;   // B persists across tiles
   static constexpr size_t OFF_A = 0;
   static constexpr size_t OFF_B = OFF_A + A_BYTES;
   static constexpr size_t OFF_Y = Y_ALIAS ? 0 : OFF_B + B_BYTES;
@@ -186,7 +233,8 @@ __host__ __device__ __forceinline__ int bf16_core_offset(int row, int k) {
   return (row >> 3) * (KP / 8) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-// scheme: 0 exact, 1 bf16x3, 2 bf16
+// scheme: 0 exact, 1 bf16x3, 2 bf16.  Persistent: each CTA loads the K_ref digits once and
+// takes tiles from a global counter until none are left.
 template <int DIM, int P, int NC, int SCHEME>
 __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double* __restrict__ u,
                                                     double* __restrict__ out, int mode) {
@@ -205,18 +253,12 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   float* xs = reinterpret_cast<float*>(smem + C::OFF_XS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // 0: B copy, 1: MMA phase 1, 2: phase 2
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 32);
+  int* next_tile = reinterpret_cast<int*>(smem + C::OFF_BAR + 40);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x;
-  const int bx = tile % pb.tc_tiles[0];
-  const int by = (tile / pb.tc_tiles[0]) % pb.tc_tiles[1];
-  const int bz = DIM == 3 ? tile / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
-  const int X0 = bx * C::TX, Y0 = by * C::TY, Z0 = bz * C::TZ;
-  const int X1 = min(X0 + C::TX, pb.n[0]), Y1 = min(Y0 + C::TY, pb.n[1]);
-  const int Z1 = DIM == 3 ? min(Z0 + C::TZ, pb.n[2]) : 1;
-  const int gx0 = (X0 - 1) * P, gy0 = (Y0 - 1) * P, gz0 = DIM == 3 ? (Z0 - 1) * P : 0;
+  const int n_tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
 
-  // ---- set-up: TMEM, barriers, K_ref digits (bulk copy), observers
+  // ---- once per CTA: TMEM, barriers, K_ref digits (bulk copy), tables, observers
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(C::TMEM_COLS));
@@ -226,7 +268,6 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[b])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("fence.proxy.async.shared::cta;");
-    // K_ref digit slices: one bulk-async copy global -> shared, completion on bars[0]
     const uint32_t bytes = (uint32_t)C::B_BYTES;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(bytes)
                  : "memory");
@@ -235,8 +276,8 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
                  "l"(pb.tc_bimg), "r"(bytes), "r"(smem_u32(&bars[0]))
                  : "memory");
   }
+  if (tid == 0) *next_tile = atomicAdd(pb.tile_counter, 1);
   for (int i = tid; i < NP; i += blockDim.x) Fr[i] = pb.tc_frow ? pb.tc_frow[i] : 0;
-  for (int i = tid; i < 128; i += blockDim.x) Eb[i] = SCHEME == 0 ? 0 : kNoScale;
   for (int j = tid; j < KP; j += blockDim.x) {
     int node = j / NC, comp = j % NC;
     int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
@@ -244,7 +285,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   }
   unsigned long long k = 0;
   if (mode == kModeCDM) k = *((volatile unsigned long long*)pb.step);
-  if (tile == 0 && mode == kModeCDM && pb.n_obs_rows > 0 && pb.ring_cap > 0) {
+  if (blockIdx.x == 0 && mode == kModeCDM && pb.n_obs_rows > 0 && pb.ring_cap > 0) {
     for (int r = tid; r < pb.n_obs_rows; r += blockDim.x) {
       double acc = 0.0;
       for (int j = 0; j < pb.obs_nodes; ++j)
@@ -252,93 +293,8 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
       pb.ring[(size_t)(k % (unsigned long long)pb.ring_cap) * pb.n_obs_rows + r] = acc;
     }
   }
-  // node patch of u^k (zero outside the lattice)
-  for (int i = tid; i < C::PATCH; i += blockDim.x) {
-    int comp = i % NC, node = i / NC;
-    int px = node % PX, py = (node / PX) % PY, pz = node / (PX * PY);
-    int gx = gx0 + px, gy = gy0 + py, gz = gz0 + pz;
-    double v = 0.0;
-    if (gx >= 0 && gx < pb.lat[0] && gy >= 0 && gy < pb.lat[1] && gz >= 0 && gz < pb.lat[2])
-      v = u[(((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp];
-    patch[i] = v;
-  }
-  __syncthreads();
-
-  // ---- per-cell row exponent (largest biased FP64 exponent of the gathered vector)
-  if (SCHEME == 0) {
-    for (int idx = tid; idx < C::NE * NL; idx += blockDim.x) {
-      int m = idx / NL, j = idx - m * NL;
-      int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-      double x = patch[((elz * P * PY + ely * P) * PX + elx * P) * NC + off[j]];
-      int eb = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-      if (eb > 0) atomicMax(&Eb[m], eb);
-    }
-    __syncthreads();
-  }
-
-  // ---- A digits: each work item writes one 8-element row of a core matrix (16 bytes)
-  // of slots 0 and 1; slices 2 and 3 of the exact scheme are kept in registers
-  constexpr int KG = KP / 8;
-  constexpr int ITEMS = 128 * KG;
-  constexpr int IPT = (ITEMS + 255) / 256;
-  uint32_t keep[IPT][8];  // packed BF16 pairs of slices 2, 3 (exact scheme)
-#pragma unroll
-  for (int it = 0; it < IPT; ++it) {
-    int item = tid + it * 256;
-    if (item >= ITEMS) break;
-    int m = item / KG, kg = item - m * KG;
-    uint16_t d[4][8];
-    int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-    const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int j = kg * 8 + q;
-      double x = (m < C::NE && j < NL) ? xe[off[j]] : 0.0;
-      if (SCHEME == 0) {
-        long long bits = __double_as_longlong(x);
-        int eb = (int)((bits >> 52) & 0x7ff);
-        long long V = 0;
-        if (eb > 0) {
-          int sh = 21 + (Eb[m] - eb);  // >= 21
-          unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-          unsigned long long mag = sh < 64 ? ((M >> (sh - 1)) + 1ull) >> 1 : 0ull;  // round half up
-          V = bits < 0 ? -(long long)mag : (long long)mag;
-        }
-        long long d0 = (V + (1ll << 23)) >> 24;
-        long long r = V - (d0 << 24);
-        long long d1 = (r + (1ll << 15)) >> 16;
-        r -= d1 << 16;
-        long long d2 = (r + (1ll << 7)) >> 8;
-        long long d3 = r - (d2 << 8);
-        d[0][q] = bf16_of_small_int((int)d0);
-        d[1][q] = bf16_of_small_int((int)d1);
-        d[2][q] = bf16_of_small_int((int)d2);
-        d[3][q] = bf16_of_small_int((int)d3);
-      } else {
-        float xf = f64_to_f32_rn(x);
-        uint16_t h = bf16_rn(xf);
-        float hf = __uint_as_float((uint32_t)h << 16);
-        d[0][q] = h;
-        d[1][q] = bf16_rn(xf - hf);
-        d[2][q] = 0;
-        d[3][q] = 0;
-      }
-    }
-    int o = bf16_core_offset<KP>(m, kg * 8);
-    uint4 s0, s1;
-    s0.x = d[0][0] | ((uint32_t)d[0][1] << 16); s0.y = d[0][2] | ((uint32_t)d[0][3] << 16);
-    s0.z = d[0][4] | ((uint32_t)d[0][5] << 16); s0.w = d[0][6] | ((uint32_t)d[0][7] << 16);
-    s1.x = d[1][0] | ((uint32_t)d[1][1] << 16); s1.y = d[1][2] | ((uint32_t)d[1][3] << 16);
-    s1.z = d[1][4] | ((uint32_t)d[1][5] << 16); s1.w = d[1][6] | ((uint32_t)d[1][7] << 16);
-    *reinterpret_cast<uint4*>(A + o) = s0;
-    *reinterpret_cast<uint4*>(A + C::A_SLICE + o) = s1;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      keep[it][q] = d[2][2 * q] | ((uint32_t)d[2][2 * q + 1] << 16);
-      keep[it][4 + q] = d[3][2 * q] | ((uint32_t)d[3][2 * q + 1] << 16);
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  double fk = 0.0;
+  if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) fk = ricker_tc((double)k * pb.dt, pb.f_e);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -347,223 +303,359 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
                          ((uint32_t)(128 >> 4) << 24);
   const uint32_t aS[2] = {smem_u32(A), smem_u32(A + C::A_SLICE)};
   const uint32_t bS0 = smem_u32(B);
-  bool ok = true;
+  bool ok = true, bimg_ready = false, bad = false;
+  constexpr int KG = KP / 8;
+  constexpr int ROWS = (C::NE + 7) / 8 * 8;   // MMA rows that carry cells (the rest are ignored)
+  constexpr int ITEMS = ROWS * KG;
+  constexpr int IPT = (ITEMS + 255) / 256;
 
-  // ---- phase 1 MMAs (A slots hold x-digit slices 0 and 1)
-  if (tid == 0) {
-    ok = mbar_wait(smem_u32(&bars[0]), 0);  // K_ref digits have landed
-    if (ok) {
-      // (s, t, level, first-in-chain)
-      const int S1 = SCHEME == 0 ? 7 : (SCHEME == 1 ? 3 : 1);
-      const int ps[7] = {0, 0, 1, 0, 1, 0, 1};
-      const int pt[7] = {0, 1, 0, 2, 1, 3, 2};
-      const int pl[7] = {0, 1, 1, 2, 2, 3, 3};
-      const int pf[7] = {1, 1, 0, 1, 0, 1, 0};
-      // bf16x3: hi.hi, hi.lo (B slice 1 = K lo), lo.hi -> all into level 0
-      const int qs[3] = {0, 0, 1};
-      const int qt[3] = {0, 1, 0};
-      for (int w = 0; w < S1; ++w) {
-        int s = SCHEME == 0 ? ps[w] : qs[w], t = SCHEME == 0 ? pt[w] : qt[w];
-        int l = SCHEME == 0 ? pl[w] : 0;
-        int first = SCHEME == 0 ? pf[w] : (w == 0);
-        uint32_t acc_addr = tmem + (uint32_t)(l * NP);
-        for (int kk = 0; kk < KP / 16; ++kk) {
-          uint64_t da = umma_desc(aS[s] + kk * 2 * C::LBO, C::LBO, C::SBO);
-          uint64_t db = umma_desc(bS0 + (uint32_t)(t * C::B_SLICE * 2) + kk * 2 * C::LBO, C::LBO, C::SBO);
-          mma_bf16(acc_addr, da, db, idesc, (first && kk == 0) ? 0u : 1u);
-        }
-      }
+  // asynchronous load of the node patch of `tile` (zero outside the lattice)
+  auto issue_patch = [&](int t) {
+    const int ibx = t % pb.tc_tiles[0];
+    const int iby = (t / pb.tc_tiles[0]) % pb.tc_tiles[1];
+    const int ibz = DIM == 3 ? t / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
+    const int hx0 = (ibx * C::TX - 1) * P, hy0 = (iby * C::TY - 1) * P;
+    const int hz0 = DIM == 3 ? (ibz * C::TZ - 1) * P : 0;
+    for (int node = tid; node < C::PATCH / NC; node += blockDim.x) {
+      int px = node % PX, py = (node / PX) % PY, pz = node / (PX * PY);
+      int gx = hx0 + px, gy = hy0 + py, gz = hz0 + pz;
+      bool in = gx >= 0 && gx < pb.lat[0] && gy >= 0 && gy < pb.lat[1] && gz >= 0 && gz < pb.lat[2];
+      int64_t g = in ? (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC : 0;
+      cp_async_zfill<8 * NC>(patch + node * NC, u + g, in ? 8 * NC : 0);
     }
-    mma_commit(smem_u32(&bars[1]));
-  }
-  if (SCHEME == 0) {
-    // slices 2 and 3 overwrite the slots once phase 1 has consumed them
-    bool r1 = mbar_wait(smem_u32(&bars[1]), 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+  for (int iter = 0;; ++iter) {
+    const int tile = *next_tile;
+    if (tile >= n_tiles) break;
+    const uint32_t par = (uint32_t)(iter & 1);
+    const int bx = tile % pb.tc_tiles[0];
+    const int by = (tile / pb.tc_tiles[0]) % pb.tc_tiles[1];
+    const int bz = DIM == 3 ? tile / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
+    const int X0 = bx * C::TX, Y0 = by * C::TY, Z0 = bz * C::TZ;
+    const int X1 = min(X0 + C::TX, pb.n[0]), Y1 = min(Y0 + C::TY, pb.n[1]);
+    const int Z1 = DIM == 3 ? min(Z0 + C::TZ, pb.n[2]) : 1;
+    const int gx0 = (X0 - 1) * P, gy0 = (Y0 - 1) * P, gz0 = DIM == 3 ? (Z0 - 1) * P : 0;
+
+    // ---- node patch of u^k: prefetched during the previous tile's update, else loaded now
+    if (iter == 0) {
+      issue_patch(tile);
+      cp_async_commit_wait_all();
+    }
+    __syncthreads();
+    if (tid == 0) *next_tile = atomicAdd(pb.tile_counter, 1);   // read after the loop-end barrier
+
+    // ---- per-cell row exponent: warp reduction of the largest biased exponent
+    if (SCHEME == 0) {
+      for (int m = warp; m < C::NE; m += 8) {
+        int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
+        const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
+        int eb = 0;
+        for (int j = lane; j < NL; j += 32) eb = max(eb, (int)((__double_as_longlong(xe[off[j]]) >> 52) & 0x7ff));
+        eb = __reduce_max_sync(0xffffffffu, eb);
+        if (lane == 0) Eb[m] = eb;
+      }
+    } else {
+      for (int m = tid; m < 128; m += blockDim.x) Eb[m] = kNoScale;
+    }
+    __syncthreads();
+
+    // ---- A digits: each item writes one 8-element row of a core matrix (16 bytes) of slots
+    // 0 and 1; slices 2 and 3 of the exact scheme stay in registers until phase 2
+    uint32_t keep[IPT][8];
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
+      // item order: 8 consecutive items fill the 8 rows of one core matrix, so a warp
+      // writes 512 contiguous bytes (no bank conflicts)
       int item = tid + it * 256;
       if (item >= ITEMS) break;
-      int m = item / KG, kg = item - m * KG;
-      int o = bf16_core_offset<KP>(m, kg * 8);
-      *reinterpret_cast<uint4*>(A + o) = make_uint4(keep[it][0], keep[it][1], keep[it][2], keep[it][3]);
-      *reinterpret_cast<uint4*>(A + C::A_SLICE + o) = make_uint4(keep[it][4], keep[it][5], keep[it][6], keep[it][7]);
+      int r8 = item & 7, rest = item >> 3;
+      int kg = rest % KG, rg = rest / KG;
+      int m = rg * 8 + r8;
+      uint32_t w[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+      if (m < C::NE && kg * 8 < NL) {
+        int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
+        const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
+        const int em = Eb[m];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int j = kg * 8 + q;
+          double x = j < NL ? xe[off[j]] : 0.0;
+          uint16_t h[4];
+          if (SCHEME == 0) {
+            int dg[4];
+            fp64_digits(x, em, dg);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) h[l] = bf16_of_small_int(dg[l]);
+          } else {
+            float xf = f64_to_f32_rn(x);
+            h[0] = bf16_rn(xf);
+            h[1] = bf16_rn(xf - __uint_as_float((uint32_t)h[0] << 16));
+            h[2] = h[3] = 0;
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) w[l][q >> 1] |= (uint32_t)h[l] << (16 * (q & 1));
+        }
+      }
+      const int o = item * 8;   // == bf16_core_offset<KP>(m, kg * 8)
+      *reinterpret_cast<uint4*>(A + o) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+      *reinterpret_cast<uint4*>(A + C::A_SLICE + o) = make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        keep[it][q] = w[2][q];
+        keep[it][4 + q] = w[3][q];
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // ---- phase 1 MMAs (A slots hold x-digit slices 0 and 1)
     if (tid == 0) {
-      if (ok && r1) {
-        // (2,0) -> level 2, (2,1) -> level 3, (3,0) -> level 3
-        const int qs2[3] = {0, 0, 1};
-        const int qt2[3] = {0, 1, 0};
-        const int ql2[3] = {2, 3, 3};
-        for (int w = 0; w < 3; ++w) {
-          uint32_t acc_addr = tmem + (uint32_t)(ql2[w] * NP);
+      if (!bimg_ready) {
+        ok = mbar_wait(smem_u32(&bars[0]), 0);  // K_ref digits have landed
+        bimg_ready = true;
+      }
+      if (ok) {
+        const int S1 = SCHEME == 0 ? 7 : (SCHEME == 1 ? 3 : 1);
+        const int ps[7] = {0, 0, 1, 0, 1, 0, 1};
+        const int pt[7] = {0, 1, 0, 2, 1, 3, 2};
+        const int pl[7] = {0, 1, 1, 2, 2, 3, 3};
+        const int pf[7] = {1, 1, 0, 1, 0, 1, 0};
+        const int qs[3] = {0, 0, 1};
+        const int qt[3] = {0, 1, 0};
+        for (int w = 0; w < S1; ++w) {
+          int s = SCHEME == 0 ? ps[w] : qs[w], t = SCHEME == 0 ? pt[w] : qt[w];
+          int l = SCHEME == 0 ? pl[w] : 0;
+          int first = SCHEME == 0 ? pf[w] : (w == 0);
+          uint32_t acc_addr = tmem + (uint32_t)(l * NP);
           for (int kk = 0; kk < KP / 16; ++kk) {
-            uint64_t da = umma_desc(aS[qs2[w]] + kk * 2 * C::LBO, C::LBO, C::SBO);
-            uint64_t db = umma_desc(bS0 + (uint32_t)(qt2[w] * C::B_SLICE * 2) + kk * 2 * C::LBO, C::LBO, C::SBO);
-            mma_bf16(acc_addr, da, db, idesc, 1u);
+            uint64_t da = umma_desc(aS[s] + kk * 2 * C::LBO, C::LBO, C::SBO);
+            uint64_t db = umma_desc(bS0 + (uint32_t)(t * C::B_SLICE * 2) + kk * 2 * C::LBO, C::LBO, C::SBO);
+            mma_bf16(acc_addr, da, db, idesc, (first && kk == 0) ? 0u : 1u);
           }
         }
       }
-      mma_commit(smem_u32(&bars[2]));
+      mma_commit(smem_u32(&bars[1]));
     }
-  }
-  const bool ready = mbar_wait(smem_u32(&bars[SCHEME == 0 ? 2 : 1]), 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ready) {
-    if (tid == 0) atomicOr(pb.flags, 2);
-  } else if (warp < 4) {
-    // ---- drain TMEM: level 0 -> yD (exact integers), levels 1-3 -> yL (FP32)
-    const int m = warp * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    bool r_all = true;
+    if (SCHEME == 0) {
+      bool r1 = mbar_wait(smem_u32(&bars[1]), par);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int it = 0; it < IPT; ++it) {
+        int item = tid + it * 256;
+        if (item >= ITEMS) break;
+        const int o = item * 8;
+        *reinterpret_cast<uint4*>(A + o) = make_uint4(keep[it][0], keep[it][1], keep[it][2], keep[it][3]);
+        *reinterpret_cast<uint4*>(A + C::A_SLICE + o) = make_uint4(keep[it][4], keep[it][5], keep[it][6], keep[it][7]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        if (ok && r1) {
+          const int qs2[3] = {0, 0, 1};
+          const int qt2[3] = {0, 1, 0};
+          const int ql2[3] = {2, 3, 3};
+          for (int w = 0; w < 3; ++w) {
+            uint32_t acc_addr = tmem + (uint32_t)(ql2[w] * NP);
+            for (int kk = 0; kk < KP / 16; ++kk) {
+              uint64_t da = umma_desc(aS[qs2[w]] + kk * 2 * C::LBO, C::LBO, C::SBO);
+              uint64_t db = umma_desc(bS0 + (uint32_t)(qt2[w] * C::B_SLICE * 2) + kk * 2 * C::LBO, C::LBO, C::SBO);
+              mma_bf16(acc_addr, da, db, idesc, 1u);
+            }
+          }
+        }
+        mma_commit(smem_u32(&bars[2]));
+      }
+      r_all = r1;
+    }
+    const bool ready = mbar_wait(smem_u32(&bars[SCHEME == 0 ? 2 : 1]), par) && r_all;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ready) {
+      if (tid == 0) atomicOr(pb.flags, 2);
+    } else if (warp < 4) {
+      // ---- drain TMEM: level 0 -> yD (exact integers), levels 1-3 -> yL (FP32)
+      const int m = warp * 32 + lane;
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < NP; c0 += 16) {
-      uint32_t r[4][16];
+      for (int c0 = 0; c0 < NP; c0 += 16) {
+        uint32_t r[4][16];
 #pragma unroll
-      for (int l = 0; l < (SCHEME == 0 ? 4 : 1); ++l) {
-        uint32_t addr = lane_base + (uint32_t)(l * NP + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]), "=r"(r[l][5]),
-              "=r"(r[l][6]), "=r"(r[l][7]), "=r"(r[l][8]), "=r"(r[l][9]), "=r"(r[l][10]), "=r"(r[l][11]),
-              "=r"(r[l][12]), "=r"(r[l][13]), "=r"(r[l][14]), "=r"(r[l][15])
-            : "r"(addr));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (m < C::NE) {
+        for (int l = 0; l < (SCHEME == 0 ? 4 : 1); ++l) {
+          uint32_t addr = lane_base + (uint32_t)(l * NP + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[l][0]), "=r"(r[l][1]), "=r"(r[l][2]), "=r"(r[l][3]), "=r"(r[l][4]), "=r"(r[l][5]),
+                "=r"(r[l][6]), "=r"(r[l][7]), "=r"(r[l][8]), "=r"(r[l][9]), "=r"(r[l][10]), "=r"(r[l][11]),
+                "=r"(r[l][12]), "=r"(r[l][13]), "=r"(r[l][14]), "=r"(r[l][15])
+              : "r"(addr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < C::NE) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          int i = c0 + q;
-          if (i < NL) {
-            yD[m * NL + i] = __uint_as_float(r[0][q]);
-            float lo = 0.f;
-            if (SCHEME == 0)
-              lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
-                        fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f, __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
-            yL[m * NL + i] = lo;
+          for (int q = 0; q < 16; ++q) {
+            int i = c0 + q;
+            if (i < NL) {
+              yD[m * NL + i] = __uint_as_float(r[0][q]);
+              float lo = 0.f;
+              if (SCHEME == 0)
+                lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
+                          fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f, __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
+              yL[m * NL + i] = lo;
+            }
           }
         }
       }
     }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
 
-  // ---- cut and outside cells replace their rows (double-FP32 on the CUDA cores)
-  for (int m = warp; m < C::NE; m += 8) {
-    int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-    int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
-    bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
-    uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
-    if (cl == 2) continue;
-    if (cl == 0) {
-      for (int i = lane; i < NL; i += 32) {
-        yD[m * NL + i] = 0.f;
-        yL[m * NL + i] = 0.f;
-      }
-      if (lane == 0) Eb[m] = kNoScale;
-      continue;
-    }
-    const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
-    float* xh = xs + warp * 2 * NL;
-    float* xl = xh + NL;
-    for (int j = lane; j < NL; j += 32) {
-      double x = xe[off[j]];
-      float h = f64_to_f32_rn(x);
-      xh[j] = h;
-      xl[j] = f64_to_f32_rn(x - f32_to_f64_scaled(h, 0));
-    }
-    __syncwarp();
-    const int64_t cell = ((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex;
-    const float* Kh = pb.Kcut32 + (size_t)pb.cut_index[cell] * 2 * NL * NL;
-    const float* Kl = Kh + NL * NL;
-    for (int i = lane; i < NL; i += 32) {
-      float s = 0.f, c = 0.f;
-      for (int j = 0; j < NL; ++j) {
-        float kh = Kh[(size_t)j * NL + i], kl = Kl[(size_t)j * NL + i];
-        float p = kh * xh[j];
-        float pe = fmaf(kh, xh[j], -p);          // exact error of the product
-        pe = fmaf(kh, xl[j], fmaf(kl, xh[j], pe));
-        float t, e;
-        two_sum(s, p, t, e);
-        s = t;
-        c += e + pe;
-      }
-      float hs, he;
-      two_sum(s, c, hs, he);
-      yD[m * NL + i] = hs;
-      yL[m * NL + i] = he;
-    }
-    __syncwarp();
-    if (lane == 0) Eb[m] = kNoScale;
-  }
-  __syncthreads();
-
-  // ---- node-centric assembly and the FP64 update (owned nodes, no runtime division)
-  const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
-  const int nox = (X1 - X0) * P + (X1 == pb.n[0] ? 1 : 0);
-  const int noy = (Y1 - Y0) * P + (Y1 == pb.n[1] ? 1 : 0);
-  const int noz = DIM == 3 ? (Z1 - Z0) * P + (Z1 == pb.n[2] ? 1 : 0) : 1;
-  constexpr int WX = C::TX * P + 1, WY = C::TY * P + 1, WZ = DIM == 3 ? C::TZ * P + 1 : 1;
-  double fk = 0.0;
-  int src_lo = 0, src_hi = 0;
-  if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) {
-    src_lo = pb.tsrc_ptr[tile];
-    src_hi = pb.tsrc_ptr[tile + 1];
-    if (src_hi > src_lo) fk = ricker_tc((double)k * pb.dt, pb.f_e);
-  }
-  bool bad = false;
-  constexpr int TOTAL = WX * WY * WZ * NC;
-  for (int i = tid; i < TOTAL; i += blockDim.x) {
-    const int comp = i % NC, node = i / NC;
-    const int lx = node % WX, ly = (node / WX) % WY, lz = node / (WX * WY);
-    if (lx >= nox || ly >= noy || lz >= noz) continue;
-    const int gx = ox0 + lx, gy = oy0 + ly, gz = oz0 + lz;
-    // patch-local coordinates: node index relative to the halo'd tile origin
-    const int px = lx + P, py = ly + P, pz = DIM == 3 ? lz + P : 0;
-    const int cx = px / P, cy = py / P, cz = DIM == 3 ? pz / P : 0;
-    const int nxe = (px % P == 0) ? 2 : 1, nye = (py % P == 0) ? 2 : 1;
-    const int nze = DIM == 3 ? ((pz % P == 0) ? 2 : 1) : 1;
-    double hi = 0.0;
-    float lo = 0.f;
-    bool first = true;
-    for (int iz = 0; iz < nze; ++iz)
-      for (int iy = 0; iy < nye; ++iy)
-        for (int ix = 0; ix < nxe; ++ix) {
-          const int ecx = cx - (nxe - 1) + ix, ecy = cy - (nye - 1) + iy, ecz = DIM == 3 ? cz - (nze - 1) + iz : 0;
-          if (ecx >= EX || ecy >= EY || (DIM == 3 && ecz >= C::EZ)) continue;
-          const int m = (ecz * EY + ecy) * EX + ecx;
-          const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
-          const int e = Eb[m];
-          const int sh = (e == kNoScale) ? 0 : e - 1023 + Fr[row] - 14;
-          double v = f32_to_f64_scaled(yD[m * NL + row], sh);
-          hi = first ? v : hi + v;
-          first = false;
-          lo += f32_scale(yL[m * NL + row], sh);
+    // ---- cut and outside cells replace their rows (double-FP32 on the CUDA cores)
+    for (int m = warp; m < C::NE; m += 8) {
+      int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
+      int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
+      bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
+      uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
+      if (cl == 2) continue;
+      if (cl == 0) {
+        for (int i = lane; i < NL; i += 32) {
+          yD[m * NL + i] = 0.f;
+          yL[m * NL + i] = 0.f;
         }
-    const int64_t dof = (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp;
-    if (mode == kModeApply) {
-      out[dof] = hi + f32_to_f64_scaled(lo, 0);
-      continue;
+        if (lane == 0) Eb[m] = kNoScale;
+        continue;
+      }
+      const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
+      float* xh = xs + warp * 2 * NL;
+      float* xl = xh + NL;
+      for (int j = lane; j < NL; j += 32) {
+        double x = xe[off[j]];
+        float h = f64_to_f32_rn(x);
+        xh[j] = h;
+        xl[j] = f64_to_f32_rn(x - f32_to_f64_scaled(h, 0));
+      }
+      __syncwarp();
+      const int64_t cell = ((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex;
+      const float* Kh = pb.Kcut32 + (size_t)pb.cut_index[cell] * 2 * NL * NL;
+      const float* Kl = Kh + NL * NL;
+      for (int i = lane; i < NL; i += 32) {
+        float sacc = 0.f, c = 0.f;
+        for (int j = 0; j < NL; ++j) {
+          float kh = Kh[(size_t)j * NL + i], kl = Kl[(size_t)j * NL + i];
+          float p = kh * xh[j];
+          float pe = fmaf(kh, xh[j], -p);          // exact error of the product
+          pe = fmaf(kh, xl[j], fmaf(kl, xh[j], pe));
+          float t, e;
+          two_sum(sacc, p, t, e);
+          sacc = t;
+          c += e + pe;
+        }
+        float hs, he;
+        two_sum(sacc, c, hs, he);
+        yD[m * NL + i] = hs;
+        yL[m * NL + i] = he;
+      }
+      __syncwarp();
+      if (lane == 0) Eb[m] = kNoScale;
     }
-    const float mh = pb.minv32[dof];
-    if (!(mh > 0.f)) continue;
-    const float ml = pb.minv32[pb.n_lat_dof + dof];
-    double t = -hi;
-    for (int s2 = src_lo; s2 < src_hi; ++s2)
-      if (pb.tsrc_dof[s2] == dof) t += pb.tsrc_val[s2] * fk;
-    const float r = f64_to_f32_rn(t) - lo;
-    const float d32 = fmaf(mh, r, ml * r);
-    if (!isfinite(d32)) bad = true;
-    const double delta = f32_to_f64_scaled(d32, 0);
-    const double uval = patch[(((gz - gz0) * PY + (gy - gy0)) * PX + (gx - gx0)) * NC + comp];
-    if (mode == kModeCDM)
-      out[dof] = fma(2.0, uval, -out[dof]) + delta;
-    else
-      out[dof] = uval - pb.dt * out[dof] + 0.5 * delta;
+    __syncthreads();
+    // the patch is free from here on: start loading the next tile's (tile index is known)
+    {
+      const int nt = *next_tile;
+      if (nt < n_tiles) issue_patch(nt);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+
+    // ---- node-centric assembly and the FP64 update (owned nodes, no runtime division)
+    const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
+    const int nox = (X1 - X0) * P + (X1 == pb.n[0] ? 1 : 0);
+    const int noy = (Y1 - Y0) * P + (Y1 == pb.n[1] ? 1 : 0);
+    const int noz = DIM == 3 ? (Z1 - Z0) * P + (Z1 == pb.n[2] ? 1 : 0) : 1;
+    constexpr int WX = C::TX * P + 1, WY = C::TY * P + 1, WZ = DIM == 3 ? C::TZ * P + 1 : 1;
+    int src_lo = 0, src_hi = 0;
+    if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) {
+      src_lo = pb.tsrc_ptr[tile];
+      src_hi = pb.tsrc_ptr[tile + 1];
+    }
+    constexpr int TOTAL = WX * WY * WZ * NC;
+    constexpr int NB = 3;   // items per thread and round: their global loads are issued together
+    for (int base = tid; base < TOTAL; base += NB * 256) {
+      int64_t dofs[NB];
+      int locs[NB];
+      bool act[NB];
+      double upv[NB], ukv[NB];
+      float mhv[NB], mlv[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int i = base + b * 256;
+        const int comp = i % NC, node = i / NC;
+        const int lx = node % WX, ly = (node / WX) % WY, lz = node / (WX * WY);
+        act[b] = i < TOTAL && lx < nox && ly < noy && lz < noz;
+        const int gx = ox0 + lx, gy = oy0 + ly, gz = oz0 + lz;
+        dofs[b] = (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp;
+        locs[b] = (((DIM == 3 ? lz : 0) * WY + ly) * WX + lx) * NC + comp;
+        upv[b] = 0.0;
+        ukv[b] = 0.0;
+        mhv[b] = 0.f;
+        mlv[b] = 0.f;
+        if (act[b] && mode != kModeApply) {
+          mhv[b] = __ldg(pb.minv32 + dofs[b]);
+          mlv[b] = __ldg(pb.minv32 + pb.n_lat_dof + dofs[b]);
+          upv[b] = out[dofs[b]];
+          ukv[b] = __ldg(u + dofs[b]);   // L2-resident: the patch buffer now holds the next tile
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (!act[b]) continue;
+        const int comp = locs[b] % NC, node = locs[b] / NC;
+        const int lx = node % WX, ly = (node / WX) % WY, lz = node / (WX * WY);
+        const int px = lx + P, py = ly + P, pz = DIM == 3 ? lz + P : 0;
+        const int cx = px / P, cy = py / P, cz = DIM == 3 ? pz / P : 0;
+        const int nxe = (px % P == 0) ? 2 : 1, nye = (py % P == 0) ? 2 : 1;
+        const int nze = DIM == 3 ? ((pz % P == 0) ? 2 : 1) : 1;
+        double hi = 0.0;
+        float lo = 0.f;
+        bool first = true;
+        for (int iz = 0; iz < nze; ++iz)
+          for (int iy = 0; iy < nye; ++iy)
+            for (int ix = 0; ix < nxe; ++ix) {
+              const int ecx = cx - (nxe - 1) + ix, ecy = cy - (nye - 1) + iy, ecz = DIM == 3 ? cz - (nze - 1) + iz : 0;
+              if (ecx >= EX || ecy >= EY || (DIM == 3 && ecz >= C::EZ)) continue;
+              const int m = (ecz * EY + ecy) * EX + ecx;
+              const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
+              const int e = Eb[m];
+              const int sh = (e == kNoScale) ? 0 : e - 1023 + Fr[row] - 14;
+              double v = f32_to_f64_scaled(yD[m * NL + row], sh);
+              hi = first ? v : hi + v;
+              first = false;
+              lo += f32_scale(yL[m * NL + row], sh);
+            }
+        const int64_t dof = dofs[b];
+        if (mode == kModeApply) {
+          out[dof] = hi + f32_to_f64_scaled(lo, 0);
+          continue;
+        }
+        if (!(mhv[b] > 0.f)) continue;
+        double t = -hi;
+        for (int s2 = src_lo; s2 < src_hi; ++s2)
+          if (pb.tsrc_dof[s2] == dof) t += pb.tsrc_val[s2] * fk;
+        const float r = f64_to_f32_rn(t) - lo;
+        const float d32 = fmaf(mhv[b], r, mlv[b] * r);
+        if (!isfinite(d32)) bad = true;
+        const double delta = f32_to_f64_scaled(d32, 0);
+        const double uval = ukv[b];
+        if (mode == kModeCDM)
+          out[dof] = fma(2.0, uval, -upv[b]) + delta;
+        else
+          out[dof] = uval - pb.dt * upv[b] + 0.5 * delta;
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // patch (prefetched), Eb, A/ybuf and next_tile are reused by the next tile
   }
   if (bad) atomicOr(pb.flags, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -572,11 +664,12 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
   }
-  if (mode == kModeCDM && tid == 0) {
+  if (tid == 0) {
     __threadfence();
     unsigned prev = atomicAdd(pb.done, 1u);
     if (prev == gridDim.x - 1) {
-      *pb.step = k + 1;
+      if (mode == kModeCDM) *pb.step = k + 1;
+      *pb.tile_counter = 0;
       *pb.done = 0u;
       __threadfence();
     }
@@ -620,9 +713,33 @@ static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* ou
     cudaError_t e = cudaFuncSetAttribute(op_tc_kernel<D, P, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_LAUNCH);
     if (e != cudaSuccess) return e;
+    // all of the unified L1/shared storage as shared memory, so that the occupancy query
+    // (and the launch) see every CTA the shared memory can hold
+    e = cudaFuncSetAttribute(op_tc_kernel<D, P, N, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     configured = true;
   }
-  int blocks = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    // resident CTAs per SM from the kernel's own limits: registers, shared memory (plus the
+    // 1 KB the runtime reserves per CTA), threads and the 512 TMEM columns
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, op_tc_kernel<D, P, N, S>);
+    if (e != cudaSuccess) return e;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (regs_warp * (256 / 32));
+    const int by_smem = smem_sm / ((int)C::SMEM_LAUNCH + 1024 + (int)fa.sharedSizeBytes);
+    per_sm = std::min(std::min(by_regs, by_smem), std::min(C::CTA_TMEM_MAX, 2048 / 256));
+    if (per_sm < 1) per_sm = 1;
+  }
+  int tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
+  int blocks = std::min(tiles, per_sm * sms);
   op_tc_kernel<D, P, N, S><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode);
   return cudaGetLastError();
 }

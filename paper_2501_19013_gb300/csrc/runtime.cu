@@ -152,6 +152,7 @@ void Handle::build_device() {
   pb.step = counters;
   pb.done = reinterpret_cast<unsigned int*>(counters + 1);
   pb.flags = reinterpret_cast<int*>(counters + 2);
+  pb.tile_counter = reinterpret_cast<int*>(counters + 3);
   op_fp64_tiles(s.dim, s.p, s.ncomp, tile);
   for (int k = 0; k < 3; ++k) pb.tiles[k] = k < s.dim ? (s.n[k] + tile[k] - 1) / tile[k] : 1;
   n_blocks = op_fp64_blocks(pb);

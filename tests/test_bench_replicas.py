@@ -1,0 +1,44 @@
+"""Multi-rank (replica) aggregation of bench.py on CPU with the gloo backend, world size 2."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    step_ms = [2.0, 3.0][rank]          # rank 1 is the slower replica
+    n_dof = [1000, 1000][rank]
+    out[rank] = bench.aggregate_replicas(step_ms, n_dof, world)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_takes_slowest_rank_and_all_dofs():
+    import torch.multiprocessing as mp
+    mgr = mp.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    for r in (0, 1):
+        step_ms, value = out[r]
+        assert step_ms == pytest.approx(3.0)
+        assert value == pytest.approx(2000 / 3e-3)
+
+
+def test_single_rank_aggregation():
+    import bench
+    step_ms, value = bench.aggregate_replicas(2.0, 1000, 1)
+    assert step_ms == 2.0 and value == pytest.approx(1000 / 2e-3)
