@@ -188,6 +188,13 @@ def aggregate_replicas(step_ms, n_dof, world, device=None):
     return step_ms, n_dof / (step_ms * 1e-3)
 
 
+# arithmetic of each variant's element operator (the state and the update are FP64 in all)
+DTYPES = {"fp64": "f64",
+          "exact": "bf16 8-bit slices, exact f32 accumulation, f64 state",
+          "bf16x3": "bf16x3, f32 accumulation, f64 state",
+          "bf16": "bf16, f32 accumulation, f64 state"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2501_19013_gb300 import ibfem as ib
@@ -326,7 +333,7 @@ def run_ours(args, rank, world, local_rank):
     launches = args.steps * len(rb["kernels"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES.get(best.split(":")[-1], "f64"), "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.n), "p": w.p, "physics": "plane strain",
                        "holes": int(len(w.holes)), "stab": "evs eps=1e-4 f_lambda=1e-2 alpha=1e-12",
                        "n_dof": n_dof, "n_uncut": inf.n_uncut, "n_cut": inf.n_cut,
@@ -347,7 +354,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precisions", default="fp64")
+    ap.add_argument("--precisions", default="fp64,exact")
     ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="cells per axis of the plate (profiling)")

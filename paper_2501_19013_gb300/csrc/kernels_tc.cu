@@ -215,7 +215,7 @@ struct TcCfg {
   static constexpr size_t OFF_Y = Y_ALIAS ? 0 : OFF_B + B_BYTES;
   static constexpr size_t OFF_PATCH = ((Y_ALIAS ? OFF_B + B_BYTES : OFF_Y + Y_BYTES) + 15) / 16 * 16;
   static constexpr size_t OFF_E = OFF_PATCH + 8 * (size_t)PATCH;           // int E[128]
-  static constexpr size_t OFF_F = OFF_E + 4 * 128;                           // int F[NP]
+  static constexpr size_t OFF_F = OFF_E + 4 * (4 + 128 + 8);                 // int F[NP]
   static constexpr size_t OFF_OFF = OFF_F + 4 * (size_t)NP;                  // int off[KP]
   static constexpr size_t OFF_XS = (OFF_OFF + 4 * (size_t)KP + 15) / 16 * 16;  // 8 warps x 2 x NL floats
   static constexpr size_t OFF_BAR = (OFF_XS + 4 * 2 * 8 * (size_t)NL + 15) / 16 * 16;
@@ -241,19 +241,24 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   using C = TcCfg<DIM, P, NC>;
   constexpr int NL = C::NL, NN1 = C::NN1, KP = C::KP, NP = C::NP;
   constexpr int EX = C::EX, EY = C::EY, PX = C::PX, PY = C::PY;
+  constexpr int NV = C::PATCH;                                // patch values
   extern __shared__ __align__(1024) unsigned char smem[];
   uint16_t* A = reinterpret_cast<uint16_t*>(smem + C::OFF_A);
   uint16_t* B = reinterpret_cast<uint16_t*>(smem + C::OFF_B);
-  float* yD = reinterpret_cast<float*>(smem + C::OFF_Y);      // level-0 part
-  float* yL = yD + C::NE * NL;                                // levels 1-3 part
+  float* yD = reinterpret_cast<float*>(smem + C::OFF_Y);      // level 0, scaled to its value
+  float* yL = yD + C::NE * NL;                                // levels 1-3, scaled
   double* patch = reinterpret_cast<double*>(smem + C::OFF_PATCH);
-  int* Eb = reinterpret_cast<int*>(smem + C::OFF_E);
+  uint2* dpatch = reinterpret_cast<uint2*>(patch);            // the same storage as 4 BF16 digits
+  int* Eb = reinterpret_cast<int*>(smem + C::OFF_E);          // Eb[0]: tile exponent; Eb[1..]: lists
   int* Fr = reinterpret_cast<int*>(smem + C::OFF_F);
   int* off = reinterpret_cast<int*>(smem + C::OFF_OFF);
   float* xs = reinterpret_cast<float*>(smem + C::OFF_XS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // 0: B copy, 1: MMA phase 1, 2: phase 2
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 32);
   int* next_tile = reinterpret_cast<int*>(smem + C::OFF_BAR + 40);
+  int* n_special = reinterpret_cast<int*>(smem + C::OFF_BAR + 44);
+  int* special = Eb + 4;                                      // cut / outside cells of the tile
+  int* wmax = Eb + 4 + 128;                                   // per-warp exponent maxima
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     const int ibz = DIM == 3 ? t / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
     const int hx0 = (ibx * C::TX - 1) * P, hy0 = (iby * C::TY - 1) * P;
     const int hz0 = DIM == 3 ? (ibz * C::TZ - 1) * P : 0;
-    for (int node = tid; node < C::PATCH / NC; node += blockDim.x) {
+    for (int node = tid; node < NV / NC; node += blockDim.x) {
       int px = node % PX, py = (node / PX) % PY, pz = node / (PX * PY);
       int gx = hx0 + px, gy = hy0 + py, gz = hz0 + pz;
       bool in = gx >= 0 && gx < pb.lat[0] && gy >= 0 && gy < pb.lat[1] && gz >= 0 && gz < pb.lat[2];
@@ -324,6 +329,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
       cp_async_zfill<8 * NC>(patch + node * NC, u + g, in ? 8 * NC : 0);
     }
   };
+
   for (int iter = 0;; ++iter) {
     const int tile = *next_tile;
     if (tile >= n_tiles) break;
@@ -334,38 +340,61 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     const int X0 = bx * C::TX, Y0 = by * C::TY, Z0 = bz * C::TZ;
     const int X1 = min(X0 + C::TX, pb.n[0]), Y1 = min(Y0 + C::TY, pb.n[1]);
     const int Z1 = DIM == 3 ? min(Z0 + C::TZ, pb.n[2]) : 1;
-    const int gx0 = (X0 - 1) * P, gy0 = (Y0 - 1) * P, gz0 = DIM == 3 ? (Z0 - 1) * P : 0;
 
     // ---- node patch of u^k: prefetched during the previous tile's update, else loaded now
     if (iter == 0) {
       issue_patch(tile);
       cp_async_commit_wait_all();
     }
+    // cut / outside cells of the halo'd tile (class byte per cell, compact list)
+    if (tid == 0) *n_special = 0;
     __syncthreads();
     if (tid == 0) *next_tile = atomicAdd(pb.tile_counter, 1);   // read after the loop-end barrier
+    if (tid < C::NE) {
+      int m = tid;
+      int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
+      int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
+      bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
+      uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
+      if (cl != 2) special[atomicAdd(n_special, 1)] = m;
+    }
 
-    // ---- per-cell row exponent: warp reduction of the largest biased exponent
+    // ---- tile exponent (largest biased FP64 exponent of the patch), then the patch is
+    // rewritten in place as four BF16 digits per value (8 bytes, like the FP64 value)
+    int em = 0;
     if (SCHEME == 0) {
-      for (int m = warp; m < C::NE; m += 8) {
-        int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-        const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
-        int eb = 0;
-        for (int j = lane; j < NL; j += 32) eb = max(eb, (int)((__double_as_longlong(xe[off[j]]) >> 52) & 0x7ff));
-        eb = __reduce_max_sync(0xffffffffu, eb);
-        if (lane == 0) Eb[m] = eb;
+      int e = 0;
+      for (int i = tid; i < NV; i += blockDim.x) e = max(e, (int)((__double_as_longlong(patch[i]) >> 52) & 0x7ff));
+      e = __reduce_max_sync(0xffffffffu, e);
+      if (lane == 0) wmax[warp] = e;
+      __syncthreads();
+      em = wmax[0];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) em = max(em, wmax[w]);
+    }
+    for (int i = tid; i < NV; i += blockDim.x) {
+      double x = patch[i];
+      uint32_t lo16, hi16;
+      if (SCHEME == 0) {
+        int dg[4];
+        fp64_digits(x, em, dg);
+        lo16 = bf16_of_small_int(dg[0]) | ((uint32_t)bf16_of_small_int(dg[1]) << 16);
+        hi16 = bf16_of_small_int(dg[2]) | ((uint32_t)bf16_of_small_int(dg[3]) << 16);
+      } else {
+        float xf = f64_to_f32_rn(x);
+        uint16_t h = bf16_rn(xf);
+        lo16 = h | ((uint32_t)bf16_rn(xf - __uint_as_float((uint32_t)h << 16)) << 16);
+        hi16 = 0;
       }
-    } else {
-      for (int m = tid; m < 128; m += blockDim.x) Eb[m] = kNoScale;
+      dpatch[i] = make_uint2(lo16, hi16);
     }
     __syncthreads();
 
-    // ---- A digits: each item writes one 8-element row of a core matrix (16 bytes) of slots
-    // 0 and 1; slices 2 and 3 of the exact scheme stay in registers until phase 2
+    // ---- A operand: each item writes one 8-element row of a core matrix (16 bytes) of slots
+    // 0 and 1 by copying digits; slices 2 and 3 stay in registers until phase 2
     uint32_t keep[IPT][8];
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
-      // item order: 8 consecutive items fill the 8 rows of one core matrix, so a warp
-      // writes 512 contiguous bytes (no bank conflicts)
       int item = tid + it * 256;
       if (item >= ITEMS) break;
       int r8 = item & 7, rest = item >> 3;
@@ -374,26 +403,16 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
       uint32_t w[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
       if (m < C::NE && kg * 8 < NL) {
         int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-        const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
-        const int em = Eb[m];
+        const uint2* xe = dpatch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          int j = kg * 8 + q;
-          double x = j < NL ? xe[off[j]] : 0.0;
-          uint16_t h[4];
-          if (SCHEME == 0) {
-            int dg[4];
-            fp64_digits(x, em, dg);
-#pragma unroll
-            for (int l = 0; l < 4; ++l) h[l] = bf16_of_small_int(dg[l]);
-          } else {
-            float xf = f64_to_f32_rn(x);
-            h[0] = bf16_rn(xf);
-            h[1] = bf16_rn(xf - __uint_as_float((uint32_t)h[0] << 16));
-            h[2] = h[3] = 0;
-          }
-#pragma unroll
-          for (int l = 0; l < 4; ++l) w[l][q >> 1] |= (uint32_t)h[l] << (16 * (q & 1));
+        for (int q = 0; q < 8; q += 2) {
+          const int j = kg * 8 + q;
+          uint2 a = j < NL ? xe[off[j]] : make_uint2(0u, 0u);
+          uint2 b = j + 1 < NL ? xe[off[j + 1]] : make_uint2(0u, 0u);
+          w[0][q >> 1] = __byte_perm(a.x, b.x, 0x5410);   // slice 0 of j and j+1
+          w[1][q >> 1] = __byte_perm(a.x, b.x, 0x7632);   // slice 1
+          w[2][q >> 1] = __byte_perm(a.y, b.y, 0x5410);   // slice 2
+          w[3][q >> 1] = __byte_perm(a.y, b.y, 0x7632);   // slice 3
         }
       }
       const int o = item * 8;   // == bf16_core_offset<KP>(m, kg * 8)
@@ -477,9 +496,11 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     if (!ready) {
       if (tid == 0) atomicOr(pb.flags, 2);
     } else if (warp < 4) {
-      // ---- drain TMEM: level 0 -> yD (exact integers), levels 1-3 -> yL (FP32)
+      // ---- drain TMEM: level 0 and the combined levels 1-3, both scaled to their value
+      // 2^(E + F_i - 14) by exponent arithmetic (exact; the exponent is the tile's)
       const int m = warp * 32 + lane;
       const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      const int ebase = em - 1023 - 14;
 #pragma unroll 1
       for (int c0 = 0; c0 < NP; c0 += 16) {
         uint32_t r[4][16];
@@ -499,12 +520,17 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
           for (int q = 0; q < 16; ++q) {
             int i = c0 + q;
             if (i < NL) {
-              yD[m * NL + i] = __uint_as_float(r[0][q]);
-              float lo = 0.f;
-              if (SCHEME == 0)
-                lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
-                          fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f, __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
-              yL[m * NL + i] = lo;
+              if (SCHEME == 0) {
+                const int sh = ebase + Fr[i];
+                float lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
+                                fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f,
+                                     __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
+                yD[m * NL + i] = f32_scale(__uint_as_float(r[0][q]), sh);
+                yL[m * NL + i] = f32_scale(lo, sh);
+              } else {
+                yD[m * NL + i] = __uint_as_float(r[0][q]);
+                yL[m * NL + i] = 0.f;
+              }
             }
           }
         }
@@ -513,26 +539,29 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
 
-    // ---- cut and outside cells replace their rows (double-FP32 on the CUDA cores)
-    for (int m = warp; m < C::NE; m += 8) {
+    // ---- cut and outside cells replace their rows (double-FP32 on the CUDA cores; u^k from
+    // global memory, the patch now holds digits)
+    const int nsp = *n_special;
+    for (int q = warp; q < nsp; q += 8) {
+      const int m = special[q];
       int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
       int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
       bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
       uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
-      if (cl == 2) continue;
       if (cl == 0) {
         for (int i = lane; i < NL; i += 32) {
           yD[m * NL + i] = 0.f;
           yL[m * NL + i] = 0.f;
         }
-        if (lane == 0) Eb[m] = kNoScale;
         continue;
       }
-      const double* xe = patch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
       float* xh = xs + warp * 2 * NL;
       float* xl = xh + NL;
       for (int j = lane; j < NL; j += 32) {
-        double x = xe[off[j]];
+        int node = j / NC, comp = j % NC;
+        int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
+        int64_t g = ((((int64_t)(ez * P + c) * pb.lat[1]) + (ey * P + b)) * pb.lat[0] + ex * P + a) * NC + comp;
+        double x = u[g];
         float h = f64_to_f32_rn(x);
         xh[j] = h;
         xl[j] = f64_to_f32_rn(x - f32_to_f64_scaled(h, 0));
@@ -559,7 +588,6 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
         yL[m * NL + i] = he;
       }
       __syncwarp();
-      if (lane == 0) Eb[m] = kNoScale;
     }
     __syncthreads();
     // the patch is free from here on: start loading the next tile's (tile index is known)
@@ -596,7 +624,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
         act[b] = i < TOTAL && lx < nox && ly < noy && lz < noz;
         const int gx = ox0 + lx, gy = oy0 + ly, gz = oz0 + lz;
         dofs[b] = (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp;
-        locs[b] = (((DIM == 3 ? lz : 0) * WY + ly) * WX + lx) * NC + comp;
+        locs[b] = i;
         upv[b] = 0.0;
         ukv[b] = 0.0;
         mhv[b] = 0.f;
@@ -627,12 +655,10 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
               if (ecx >= EX || ecy >= EY || (DIM == 3 && ecz >= C::EZ)) continue;
               const int m = (ecz * EY + ecy) * EX + ecx;
               const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
-              const int e = Eb[m];
-              const int sh = (e == kNoScale) ? 0 : e - 1023 + Fr[row] - 14;
-              double v = f32_to_f64_scaled(yD[m * NL + row], sh);
+              double v = f32_to_f64_scaled(yD[m * NL + row], 0);
               hi = first ? v : hi + v;
               first = false;
-              lo += f32_scale(yL[m * NL + row], sh);
+              lo += yL[m * NL + row];
             }
         const int64_t dof = dofs[b];
         if (mode == kModeApply) {
@@ -655,7 +681,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
       }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();   // patch (prefetched), Eb, A/ybuf and next_tile are reused by the next tile
+    __syncthreads();   // patch (prefetched), lists, A/ybuf and next_tile are reused by the next tile
   }
   if (bad) atomicOr(pb.flags, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
