@@ -152,6 +152,31 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Continuous batching of a seeded Poisson stream of mixed 2D/3D requests through the
+    batched exact tensor-core path; returns the latency / throughput summary."""
+    from paper_2501_19013_gb300 import workloads as W
+    from paper_2501_19013_gb300.serve import Request, Server, TcBackend
+    n = args.serve_requests
+    arr = W.poisson_arrivals(n, args.serve_rate, seed=0)
+    reqs = []
+    for i in range(n):
+        w = W.serving_request(i)
+        reqs.append(Request(rid=i, arrival=float(arr[i]), workload=w, steps=w.steps))
+    be = TcBackend()
+    srv = Server(be, hbm_budget=int(args.serve_budget_gb * (1 << 30)), max_members=args.serve_slots,
+                 chunk=32, max_pending=2, workers=8)
+    st = srv.run(reqs)
+    be.close()
+    out = st.summary()
+    out.update({"rate_per_s": args.serve_rate, "hbm_budget_gb": args.serve_budget_gb,
+                "slots": args.serve_slots, "precision": "exact",
+                "mix": "seeded: 70% 2D plates 32^2-256^2 p2-4 scalar/plane strain with 1-12 holes, "
+                       "30% 3D porous cubes 16^3-48^3 p2-3; 500-5000 steps; dt = 0.9 dt_crit each",
+                "latency": "arrival -> observer series on the host (includes host setup and dt_crit)"})
+    return out
+
+
 def parse_variant(v, w):
     """'fp64' | 'exact' | 'bf16x3' | 'bf16' -> CDM with the workload's stabilisation;
     'imex' -> Newmark IMEX (FP64); 'ms:<precision>' -> CDM with mass scaling."""
@@ -344,6 +369,8 @@ def run_ours(args, rank, world, local_rank):
             "clocks": rb["clocks"], "variants": variants_out}
     for r in results.values():
         r["solver"].close()
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -361,6 +388,10 @@ def main():
     ap.add_argument("--dt", type=float, default=0.0, help="fixed dt instead of 0.9 dt_crit (profiling)")
     ap.add_argument("--run-steps", type=int, default=-1, help="steps of the accuracy run (-1: the workload's)")
     ap.add_argument("--run-time", type=float, default=0.0, help="simulated time of the accuracy run (overrides steps)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving run (0: none)")
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrival rate of the serving run (1/s)")
+    ap.add_argument("--serve-slots", type=int, default=32, help="maximum concurrent members of the batch")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory budget of the serving run")
     ap.add_argument("--workload", default="plate_holes_elastic",
                     choices=["plate_holes_elastic", "plate_holes_imex", "porous_voxel", "plate_one_hole"])
     args = ap.parse_args()

@@ -126,7 +126,8 @@ typedef struct {
     int64_t step;             /* steps taken since set_initial / set_state             */
     double t, dt;
     double lambda_ref;        /* lambda_max(K_ref, M_ref) of one uncut cell            */
-    size_t device_bytes;      /* device memory held by the handle                      */
+    size_t device_bytes;      /* device memory held by the handle; for a host_only
+                                 handle the bytes ibfem_upload would allocate            */
 } ibfem_info_t;
 
 /* ---- lifetime -------------------------------------------------------------------- */
@@ -219,6 +220,68 @@ int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells);
 /* Element stiffness (n_loc x n_loc, row-major) used for cell `cell` (shared reference
  * matrix for uncut cells); optional lumped diagonal (n_loc). Errors: ARG (outside).   */
 int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml);
+
+/* ---- deferred upload ----------------------------------------------------------------- */
+
+/* Move a handle created with host_only = 1 onto its device: the buffers, the K_ref image
+ * and the tables that ibfem_create uploads for a device handle (its options are those given
+ * at creation).  Before the call, ibfem_info(h).device_bytes is the number of bytes this
+ * call allocates (sources, observers and the IMEX factor come on top), so a caller can
+ * admit work by device-memory footprint before any allocation happens.  This is a part of
+ * this library; the paper has no counterpart.
+ * Errors: STATE (not host_only), ARG (no kernel for the shape/precision), OOM, CUDA; on an
+ * error the handle stays host_only and holds no device memory.                          */
+int ibfem_upload(ibfem_t* h);
+
+/* ---- batched stepping (continuous batching) ------------------------------------------ */
+
+/* A batch advances many independent handles together: per shape class (dim, p, ncomp)
+ * one persistent tensor-core launch per time step covers the tiles of every member, the
+ * classes run concurrently, and chunks of 32 steps are replayed as CUDA graphs.  Members
+ * join and leave between chunks.  Each member performs exactly the arithmetic of
+ * ibfem_step on its own (same kernel code per tile, Eq. cdm), so its results do not depend
+ * on the other members.  This is a part of this library; the paper has no counterpart.
+ *
+ * Members must be device handles with precision IBFEM_EXACT_TC and scheme IBFEM_CDM, with
+ * dt and the initial state set.  While a handle is a member, every other call on it returns
+ * IBFEM_ERR_STATE, except ibfem_info and ibfem_destroy (which first waits for the batch's
+ * queued work and takes the handle out).  A batch is used from one thread at a time.     */
+typedef struct ibfem_batch_s ibfem_batch_t;
+
+/* New empty batch on `device`; `stream` (cudaStream_t, NULL = a private stream) carries
+ * its work.  Errors: CUDA.                                                              */
+int ibfem_batch_create(void* stream, int device, ibfem_batch_t** out);
+
+/* Admit handle h for n_steps (>= 1) more steps.  The batch's work starts after everything
+ * already queued on h's stream.  The K_ref image is shared with members whose image is
+ * byte-identical.  Errors: ARG (wrong precision/scheme/device, n_steps < 1), STATE (host_only,
+ * not initialised, already a member), CUDA.                                               */
+int ibfem_batch_add(ibfem_batch_t* b, ibfem_t* h, int64_t n_steps);
+
+/* Enqueue n batched steps (asynchronous).  A member whose budget runs out inside the n
+ * steps stops there exactly (its tiles are skipped afterwards) and becomes "finished":
+ * it leaves the batch, and its own stream is ordered after the batch work queued so far,
+ * so that ibfem_sample / get_state on it see its final state.  Errors: CUDA.             */
+int ibfem_batch_run(ibfem_batch_t* b, int64_t n);
+
+/* Hand back up to max_done finished handles (in completion order) in done[]; *n_done
+ * receives their count.  The handles are ordinary handles again (the caller owns them).  */
+int ibfem_batch_poll(ibfem_batch_t* b, ibfem_t** done, int max_done, int* n_done);
+
+/* Members still stepping, finished members not yet polled, batched steps enqueued.      */
+int ibfem_batch_status(const ibfem_batch_t* b, int* n_active, int* n_finished, int64_t* steps_enqueued);
+
+/* Block until at most max_pending enqueued chunks (ibfem_batch_run calls are split into
+ * chunks of up to 32 steps) are still unfinished on the GPU: the back-pressure of a
+ * serving loop, so that new members are not queued behind a long backlog.  Errors: ARG, CUDA. */
+int ibfem_batch_wait(ibfem_batch_t* b, int max_pending);
+
+/* Wait for the batch's queued work.  Errors: CUDA.                                       */
+int ibfem_batch_sync(ibfem_batch_t* b);
+
+/* Wait for the queued work, release members still in the batch (at the step their device
+ * counter reached) and free the batch.                                                   */
+int ibfem_batch_destroy(ibfem_batch_t* b);
 
 /* ---- allocation-free operator ----------------------------------------------------- */
 

@@ -58,6 +58,22 @@ struct DevProblem {
   double imex_c2;           // (1 - gamma) dt
 };
 
+// One problem of a batched tensor-core launch: its descriptor, its two state buffers and
+// the step at which it stops.  The state u^k lives in Ua for even k and in Ub for odd k,
+// so that a member's buffers do not depend on when it joined the batch.
+struct BatchMember {
+  DevProblem pb;
+  double* Ua;
+  double* Ub;
+  unsigned long long step_end;   // tiles of a member with step >= step_end are skipped
+};
+
+// Launch-wide counters of a batched launch (reset by its last CTA).
+struct BatchCtl {
+  int tile_counter;
+  unsigned int done;
+};
+
 // Device view of the IMEX partition and factor (kernels_imex.cu).
 struct ImexDev {
   int n_cells;               // cells touching the c-set
@@ -114,6 +130,10 @@ int op_fp64_blocks(const DevProblem& pb);
 // scheme: 0 exact digit slices, 1 bf16 hi/lo three-pass, 2 bf16 one pass
 cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme,
                          cudaStream_t st);
+// Batched launch (exact scheme, CDM): every member advances one step; members[m] owns the
+// global tiles [tile_start[m], tile_start[m + 1]).
+cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, const BatchMember* members, const int* tile_start,
+                               int n_members, int total_tiles, BatchCtl* ctl, cudaStream_t st);
 bool op_tc_supported(int dim, int p, int ncomp);
 void op_tc_tiles(int dim, int p, int ncomp, int* tile);
 void op_tc_dims(int dim, int p, int ncomp, int* kp, int* np);

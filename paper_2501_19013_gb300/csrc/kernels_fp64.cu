@@ -354,13 +354,10 @@ template <int D, int P, int N>
 static cudaError_t launch_op_t(const DevProblem& pb, OpInput x, double* out, int mode,
                                double* partials, cudaStream_t st) {
   using C = FusedCfg<D, P, N>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(op_fp64_kernel<D, P, N>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // thread-safe one-time configuration (function-local static initialisation)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(op_fp64_kernel<D, P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (configured != cudaSuccess) return configured;
   op_fp64_kernel<D, P, N><<<op_fp64_blocks(pb), 256, C::SMEM, st>>>(pb, x, out, mode, partials);
   return cudaGetLastError();
 }

@@ -134,7 +134,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-constexpr int kNoScale = -100000;  // E_m marker: rows whose (D0, L) are already scaled
 
 // Asynchronous copy global -> shared of 8 or 16 bytes; src_bytes = 0 writes zeros.
 template <int BYTES>
@@ -235,9 +234,15 @@ __host__ __device__ __forceinline__ int bf16_core_offset(int row, int k) {
 
 // scheme: 0 exact, 1 bf16x3, 2 bf16.  Persistent: each CTA loads the K_ref digits once and
 // takes tiles from a global counter until none are left.
-template <int DIM, int P, int NC, int SCHEME>
-__global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double* __restrict__ u,
-                                                    double* __restrict__ out, int mode) {
+// BATCH: the tiles of several problems (members) of one shape in one launch, CDM mode.  A
+// CTA keeps the descriptor of its current member in shared memory and reloads the K_ref
+// image only when a member with another image comes up (the host orders members by image).
+template <int DIM, int P, int NC, int SCHEME, bool BATCH>
+__global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevProblem pb_arg, const double* u_arg,
+                                                    double* out_arg, int mode,
+                                                    const BatchMember* __restrict__ members,
+                                                    const int* __restrict__ tile_start, int n_members,
+                                                    int total_tiles, BatchCtl* ctl) {
   using C = TcCfg<DIM, P, NC>;
   constexpr int NL = C::NL, NN1 = C::NN1, KP = C::KP, NP = C::NP;
   constexpr int EX = C::EX, EY = C::EY, PX = C::PX, PY = C::PY;
@@ -259,9 +264,25 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   int* n_special = reinterpret_cast<int*>(smem + C::OFF_BAR + 44);
   int* special = Eb + 4;                                      // cut / outside cells of the tile
   int* wmax = Eb + 4 + 128;                                   // per-warp exponent maxima
+  int* next_member = n_special + 1;                           // batched: member of next_tile
+  BatchMember* sbm = reinterpret_cast<BatchMember*>(smem + C::SMEM);  // batched: current member
+  const DevProblem& pb = BATCH ? sbm->pb : pb_arg;
+  const double* __restrict__ u = u_arg;
+  double* __restrict__ out = out_arg;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n_tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
+  const int n_tiles = BATCH ? total_tiles : pb_arg.tc_tiles[0] * pb_arg.tc_tiles[1] * pb_arg.tc_tiles[2];
+  int* const tcount = BATCH ? &ctl->tile_counter : pb_arg.tile_counter;
+  // batched: the member of global tile g (binary search of the tile ranges)
+  auto member_of = [&](int g) {
+    int lo = 0, hi = n_members;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tile_start[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    return lo;
+  };
 
   // ---- once per CTA: TMEM, barriers, K_ref digits (bulk copy), tables, observers
   if (warp == 0) {
@@ -273,6 +294,8 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[b])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("fence.proxy.async.shared::cta;");
+  }
+  if (!BATCH && tid == 32) {
     const uint32_t bytes = (uint32_t)C::B_BYTES;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(bytes)
                  : "memory");
@@ -281,16 +304,21 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
                  "l"(pb.tc_bimg), "r"(bytes), "r"(smem_u32(&bars[0]))
                  : "memory");
   }
-  if (tid == 0) *next_tile = atomicAdd(pb.tile_counter, 1);
-  for (int i = tid; i < NP; i += blockDim.x) Fr[i] = pb.tc_frow ? pb.tc_frow[i] : 0;
+  if (tid == 0) {
+    const int g = atomicAdd(tcount, 1);
+    *next_tile = g;
+    if (BATCH) *next_member = g < n_tiles ? member_of(g) : 0;
+  }
+  if (!BATCH)
+    for (int i = tid; i < NP; i += blockDim.x) Fr[i] = pb.tc_frow ? pb.tc_frow[i] : 0;
   for (int j = tid; j < KP; j += blockDim.x) {
     int node = j / NC, comp = j % NC;
     int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
     off[j] = j < NL ? ((c * PY + b) * PX + a) * NC + comp : -1;
   }
   unsigned long long k = 0;
-  if (mode == kModeCDM) k = *((volatile unsigned long long*)pb.step);
-  if (blockIdx.x == 0 && mode == kModeCDM && pb.n_obs_rows > 0 && pb.ring_cap > 0) {
+  if (!BATCH && mode == kModeCDM) k = *((volatile unsigned long long*)pb.step);
+  if (!BATCH && blockIdx.x == 0 && mode == kModeCDM && pb.n_obs_rows > 0 && pb.ring_cap > 0) {
     for (int r = tid; r < pb.n_obs_rows; r += blockDim.x) {
       double acc = 0.0;
       for (int j = 0; j < pb.obs_nodes; ++j)
@@ -299,7 +327,8 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     }
   }
   double fk = 0.0;
-  if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) fk = ricker_tc((double)k * pb.dt, pb.f_e);
+  if (!BATCH && (mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0)
+    fk = ricker_tc((double)k * pb.dt, pb.f_e);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -308,7 +337,11 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
                          ((uint32_t)(128 >> 4) << 24);
   const uint32_t aS[2] = {smem_u32(A), smem_u32(A + C::A_SLICE)};
   const uint32_t bS0 = smem_u32(B);
-  bool ok = true, bimg_ready = false, bad = false;
+  bool ok = true, bimg_ready = false, bad = false, have_patch = false;
+  int cur_m = -1;                       // batched: member whose descriptor is in shared memory
+  const uint16_t* cur_bimg = nullptr;   // batched: K_ref image in shared memory
+  uint32_t b_loads = BATCH ? 0u : 1u;   // K_ref image loads issued (phase of bars[0])
+  uint32_t mma_phase = 0;               // tiles whose MMAs were committed (phase of bars[1], bars[2])
   constexpr int KG = KP / 8;
   constexpr int ROWS = (C::NE + 7) / 8 * 8;   // MMA rows that carry cells (the rest are ignored)
   constexpr int ITEMS = ROWS * KG;
@@ -330,10 +363,46 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     }
   };
 
-  for (int iter = 0;; ++iter) {
-    const int tile = *next_tile;
-    if (tile >= n_tiles) break;
-    const uint32_t par = (uint32_t)(iter & 1);
+  for (;;) {
+    const int gt = *next_tile;
+    if (gt >= n_tiles) break;
+    int tile = gt;
+    bool skip = false;
+    if constexpr (BATCH) {
+      const int m = *next_member;
+      if (m != cur_m) {
+        // switch members (nothing reads the old descriptor after the loop-end barrier)
+        if (tid == 0) *sbm = members[m];
+        __syncthreads();
+        k = *((volatile unsigned long long*)sbm->pb.step);
+        if (k < sbm->step_end && sbm->pb.tc_bimg != cur_bimg) {
+          // new K_ref image (only for a member that still steps, so that a load is always
+          // waited on before the next one): every MMA of the previous tile has completed
+          cur_bimg = sbm->pb.tc_bimg;
+          ++b_loads;
+          bimg_ready = false;
+          if (tid == 0) {
+            const uint32_t bytes = (uint32_t)C::B_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(B)),
+                "l"(cur_bimg), "r"(bytes), "r"(smem_u32(&bars[0]))
+                : "memory");
+          }
+          for (int i = tid; i < NP; i += blockDim.x) Fr[i] = sbm->pb.tc_frow[i];
+        }
+        fk = (sbm->pb.tsrc_ptr && sbm->pb.f_e > 0.0) ? ricker_tc((double)k * sbm->pb.dt, sbm->pb.f_e) : 0.0;
+        u = (k & 1ull) ? sbm->Ub : sbm->Ua;
+        out = (k & 1ull) ? sbm->Ua : sbm->Ub;
+        cur_m = m;
+        have_patch = false;
+      }
+      tile = gt - tile_start[m];
+      skip = k >= sbm->step_end;
+    }
+    const uint32_t par = mma_phase & 1u;
     const int bx = tile % pb.tc_tiles[0];
     const int by = (tile / pb.tc_tiles[0]) % pb.tc_tiles[1];
     const int bz = DIM == 3 ? tile / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
@@ -342,14 +411,31 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     const int Z1 = DIM == 3 ? min(Z0 + C::TZ, pb.n[2]) : 1;
 
     // ---- node patch of u^k: prefetched during the previous tile's update, else loaded now
-    if (iter == 0) {
+    if (!have_patch && !skip) {
       issue_patch(tile);
       cp_async_commit_wait_all();
     }
     // cut / outside cells of the halo'd tile (class byte per cell, compact list)
     if (tid == 0) *n_special = 0;
     __syncthreads();
-    if (tid == 0) *next_tile = atomicAdd(pb.tile_counter, 1);   // read after the loop-end barrier
+    if (tid == 0) {   // read after the loop-end barrier
+      const int g = atomicAdd(tcount, 1);
+      *next_tile = g;
+      if (BATCH) *next_member = g < n_tiles ? member_of(g) : 0;
+    }
+    if (skip) {   // batched: this member has taken all its steps
+      have_patch = false;
+      __syncthreads();
+      continue;
+    }
+    if (BATCH && tile == 0 && pb.n_obs_rows > 0 && pb.ring_cap > 0) {
+      for (int r = tid; r < pb.n_obs_rows; r += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < pb.obs_nodes; ++j)
+          acc += pb.obs_w[(size_t)r * pb.obs_nodes + j] * u[pb.obs_dof[(size_t)r * pb.obs_nodes + j]];
+        pb.ring[(size_t)(k % (unsigned long long)pb.ring_cap) * pb.n_obs_rows + r] = acc;
+      }
+    }
     if (tid < C::NE) {
       int m = tid;
       int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
@@ -432,7 +518,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     // ---- phase 1 MMAs (A slots hold x-digit slices 0 and 1)
     if (tid == 0) {
       if (!bimg_ready) {
-        ok = mbar_wait(smem_u32(&bars[0]), 0);  // K_ref digits have landed
+        ok = mbar_wait(smem_u32(&bars[0]), (b_loads - 1u) & 1u);  // K_ref digits have landed
         bimg_ready = true;
       }
       if (ok) {
@@ -593,7 +679,8 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
     // the patch is free from here on: start loading the next tile's (tile index is known)
     {
       const int nt = *next_tile;
-      if (nt < n_tiles) issue_patch(nt);
+      have_patch = nt < n_tiles && (!BATCH || *next_member == cur_m);
+      if (have_patch) issue_patch(BATCH ? nt - tile_start[cur_m] : nt);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
 
@@ -680,10 +767,15 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
           out[dof] = uval - pb.dt * upv[b] + 0.5 * delta;
       }
     }
+    if (BATCH && bad) {
+      atomicOr(pb.flags, 1);
+      bad = false;
+    }
+    ++mma_phase;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();   // patch (prefetched), lists, A/ybuf and next_tile are reused by the next tile
   }
-  if (bad) atomicOr(pb.flags, 1);
+  if (!BATCH && bad) atomicOr(pb.flags, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -692,11 +784,20 @@ __global__ void __launch_bounds__(256) op_tc_kernel(DevProblem pb, const double*
   }
   if (tid == 0) {
     __threadfence();
-    unsigned prev = atomicAdd(pb.done, 1u);
+    unsigned int* const donep = BATCH ? &ctl->done : pb_arg.done;
+    unsigned prev = atomicAdd(donep, 1u);
     if (prev == gridDim.x - 1) {
-      if (mode == kModeCDM) *pb.step = k + 1;
-      *pb.tile_counter = 0;
-      *pb.done = 0u;
+      if constexpr (BATCH) {
+        for (int m = 0; m < n_members; ++m) {
+          unsigned long long* sp = members[m].pb.step;
+          const unsigned long long km = *((volatile unsigned long long*)sp);
+          if (km < members[m].step_end) *sp = km + 1;
+        }
+      } else {
+        if (mode == kModeCDM) *pb_arg.step = k + 1;
+      }
+      *tcount = 0;
+      *donep = 0u;
       __threadfence();
     }
   }
@@ -731,43 +832,67 @@ int op_tc_core_offset(int kp, int row, int k) {
   return (row >> 3) * (kp / 8) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
+// Resident CTAs per SM of one instantiation, from the kernel's own limits: registers,
+// shared memory (plus the 1 KB the runtime reserves per CTA), threads and the 512 TMEM
+// columns.  Also raises the dynamic shared memory limit and the carveout (all of the unified
+// L1/shared storage as shared memory).  Returns 0 on failure.
+template <typename KernelT>
+static int tc_configure(KernelT kernel, size_t smem_launch, int tmem_max) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_launch) != cudaSuccess)
+    return 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = regs_sm / (regs_warp * (256 / 32));
+  const int by_smem = smem_sm / ((int)smem_launch + 1024 + (int)fa.sharedSizeBytes);
+  int per_sm = std::min(std::min(by_regs, by_smem), std::min(tmem_max, 2048 / 256));
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * sms;
+}
+
 template <int D, int P, int N, int S>
 static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* out, int mode, cudaStream_t st) {
   using C = TcCfg<D, P, N>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(op_tc_kernel<D, P, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM_LAUNCH);
-    if (e != cudaSuccess) return e;
-    // all of the unified L1/shared storage as shared memory, so that the occupancy query
-    // (and the launch) see every CTA the shared memory can hold
-    e = cudaFuncSetAttribute(op_tc_kernel<D, P, N, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  static int per_sm = 0, sms = 0;
-  if (per_sm == 0) {
-    // resident CTAs per SM from the kernel's own limits: registers, shared memory (plus the
-    // 1 KB the runtime reserves per CTA), threads and the 512 TMEM columns
-    int dev = 0, smem_sm = 0, regs_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, op_tc_kernel<D, P, N, S>);
-    if (e != cudaSuccess) return e;
-    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-    const int by_regs = regs_sm / (regs_warp * (256 / 32));
-    const int by_smem = smem_sm / ((int)C::SMEM_LAUNCH + 1024 + (int)fa.sharedSizeBytes);
-    per_sm = std::min(std::min(by_regs, by_smem), std::min(C::CTA_TMEM_MAX, 2048 / 256));
-    if (per_sm < 1) per_sm = 1;
-  }
+  // thread-safe one-time configuration (function-local static initialisation)
+  static const int resident = tc_configure(op_tc_kernel<D, P, N, S, false>, C::SMEM_LAUNCH, C::CTA_TMEM_MAX);
+  if (resident == 0) return cudaErrorInvalidConfiguration;
   int tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
-  int blocks = std::min(tiles, per_sm * sms);
-  op_tc_kernel<D, P, N, S><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode);
+  int blocks = std::min(tiles, resident);
+  op_tc_kernel<D, P, N, S, false><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode, nullptr, nullptr, 0, 0,
+                                                                      nullptr);
   return cudaGetLastError();
+}
+
+template <int D, int P, int N>
+static cudaError_t launch_tc_batch_t(const BatchMember* members, const int* tile_start, int n_members,
+                                     int total_tiles, BatchCtl* ctl, cudaStream_t st) {
+  using C = TcCfg<D, P, N>;
+  constexpr size_t smem = std::max(C::SMEM + (sizeof(BatchMember) + 15) / 16 * 16, C::SMEM_FLOOR);
+  static const int resident = tc_configure(op_tc_kernel<D, P, N, 0, true>, smem, C::CTA_TMEM_MAX);
+  if (resident == 0) return cudaErrorInvalidConfiguration;
+  if (total_tiles <= 0) return cudaSuccess;
+  int blocks = std::min(total_tiles, resident);
+  DevProblem none{};
+  op_tc_kernel<D, P, N, 0, true><<<blocks, 256, smem, st>>>(none, nullptr, nullptr, kModeCDM, members, tile_start,
+                                                            n_members, total_tiles, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, const BatchMember* members, const int* tile_start,
+                               int n_members, int total_tiles, BatchCtl* ctl, cudaStream_t st) {
+#define X(D, P, N) \
+  if (dim == D && p == P && ncomp == N) return launch_tc_batch_t<D, P, N>(members, tile_start, n_members, total_tiles, ctl, st);
+  IBFEM_TC_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme,

@@ -207,6 +207,8 @@ void Handle::build_device() {
     }
     pb.tc_bimg = upload(img);
     pb.tc_frow = upload(frow);
+    tc_img_host = img;
+    tc_frow_host = frow;
     std::vector<float> k32(2 * (size_t)s.n_cut * s.n_loc * s.n_loc);
     const size_t nl2 = (size_t)s.n_loc * s.n_loc;
     for (int64_t c = 0; c < s.n_cut; ++c)
@@ -234,6 +236,38 @@ void Handle::build_device() {
   lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
   scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
   check(cudaStreamSynchronize(stream), "setup sync");
+}
+
+size_t Handle::planned_device_bytes() const {
+  const Setup& s = setup;
+  auto arr = [](int64_t count, size_t elem) { return (size_t)std::max<int64_t>(count, 1) * elem; };
+  const int64_t nl = s.n_loc, nlat = s.n_lat_dof, ncut = s.n_cut, nel = s.n_elem;
+  size_t b = 0;
+  b += arr(nel, 1) + arr(nel, 4) + arr(ncut, 8);          // cls, cut_index, cut_cells
+  b += arr(nl * nl, 8) + arr(ncut * nl * nl, 8);          // Kref, Kcut
+  b += arr(ncut, 8) * nl;                                 // Ycut
+  b += 2 * arr(nlat, 8);                                  // minv, sinv
+  if (imex) {
+    const ImexData& I = imex_host;
+    const int64_t ncell = (int64_t)I.ccells.size();
+    b += arr(ncell, 8) + arr(ncell, 8) * nl + arr((int64_t)I.comp_ptr.size(), 4) + arr((int64_t)I.g_ptr.size(), 8) +
+         arr((int64_t)I.g_idx.size(), 4) + 3 * arr(I.n_c, 8) + arr((int64_t)I.perm.size(), 8) +
+         arr((int64_t)I.c_dof.size(), 8);
+  }
+  b += 3 * arr(nlat, 8) + 32;                             // U[2], W, counters
+  int t[3] = {1, 1, 1};
+  op_fp64_tiles(s.dim, s.p, s.ncomp, t);
+  int64_t nb = 1;
+  for (int k = 0; k < s.dim; ++k) nb *= (s.n[k] + t[k] - 1) / t[k];
+  b += 2 * (size_t)nb * 8;                                // partials
+  if (opt.precision != IBFEM_FP64) {
+    int kp = 0, np = 0;
+    op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
+    b += 4 * (size_t)kp * np * 2 + arr(np, 4);            // K_ref image, row exponents
+    b += arr(2 * ncut * nl * nl, 4) + arr(2 * nlat, 4);   // Kcut32, minv32
+  }
+  b += 64 + kPowerChunk * 8 + arr(nlat, 8);               // scalars, lam_hist, scratch
+  return b;
 }
 
 void Handle::imex_upload_factor() {
@@ -412,6 +446,27 @@ namespace ibfem {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace ibfem
 
+namespace {
+void check_shape_supported(int dim, int p, int physics, int precision) {
+  const int nc = physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1;
+  if (!op_fp64_supported(dim, p, nc)) throw std::invalid_argument("no kernel instantiation for this (dim, p, ncomp)");
+  if (precision != IBFEM_FP64 && !op_tc_supported(dim, p, nc))
+    throw std::invalid_argument("no tensor-core kernel instantiation for this (dim, p, ncomp)");
+}
+
+// device half of ibfem_create (and of ibfem_upload for a host-only handle)
+void attach_device(ibfem_t* h) {
+  check(cudaSetDevice(h->opt.device), "cudaSetDevice");
+  h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  if (!h->stream) {
+    // graphs cannot be captured on the legacy stream: use a private one
+    check(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    h->own_stream = true;
+  }
+  h->build_device();
+}
+}  // namespace
+
 extern "C" {
 
 const char* ibfem_last_error(void) { return g_last_error.c_str(); }
@@ -454,9 +509,6 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
       o.precision != IBFEM_BF16_TC)
     throw std::invalid_argument("precision not supported by this build");
-  if (o.precision != IBFEM_FP64 && !o.host_only &&
-      !op_tc_supported(grid->dim, p, o.physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1))
-    throw std::invalid_argument("no tensor-core kernel instantiation for this (dim, p, ncomp)");
   if (!(o.rho > 0)) throw std::invalid_argument("rho must be > 0");
   if (stab) {
     in.stab = stab->kind;
@@ -489,30 +541,43 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
       throw std::invalid_argument("unknown geometry kind");
     }
   }
-  if (!o.host_only && !op_fp64_supported(in.dim, in.p, in.physics == IBFEM_ELASTIC_PLANE_STRAIN ? 2 : 1))
-    throw std::invalid_argument("no kernel instantiation for this (dim, p, ncomp)");
+  if (!o.host_only) check_shape_supported(in.dim, in.p, in.physics, o.precision);
   h->setup = build_setup(in);
   if (o.scheme == IBFEM_IMEX) {
     imex_partition(h->setup, h->imex_host);
     h->imex = h->imex_host.n_c > 0;   // without cut cells IMEX is the CDM
   }
-  if (!o.host_only) {
-    check(cudaSetDevice(o.device), "cudaSetDevice");
-    h->stream = static_cast<cudaStream_t>(o.stream);
-    if (!h->stream) {
-      // graphs cannot be captured on the legacy stream: use a private one
-      check(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
-      h->own_stream = true;
-    }
-    h->build_device();
-  }
+  if (!o.host_only) attach_device(h.get());
   *out = h.release();
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_upload(ibfem_t* h) {
+  if (!h) return fail(IBFEM_ERR_ARG, "null handle");
+  if (!h->opt.host_only) return fail(IBFEM_ERR_STATE, "handle is already on the device");
+  IBFEM_TRY
+  check_shape_supported(h->input.dim, h->input.p, h->input.physics, h->opt.precision);
+  h->opt.host_only = 0;
+  try {
+    attach_device(h);
+  } catch (...) {
+    // back to a host-only handle: release what was allocated
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->dfree_all();
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+    h->own_stream = false;
+    h->opt.host_only = 1;
+    throw;
+  }
   return IBFEM_OK;
   IBFEM_CATCH
 }
 
 int ibfem_destroy(ibfem_t* h) {
   if (!h) return IBFEM_OK;
+  if (h->batch) batch_forget(h);   // drains the batch stream, then drops the member
   if (!h->opt.host_only) {
     cudaSetDevice(h->opt.device);
     cudaStreamSynchronize(h->stream);
@@ -547,13 +612,14 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
     out->nnz_L = (int64_t)h->imex_host.chol.Lx.size();
     out->n_levels = (int32_t)h->imex_host.chol.fwd_level_ptr.size() - 1;
   }
-  out->device_bytes = h->device_bytes;
+  out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes;
   return IBFEM_OK;
 }
 
 static int require_device(ibfem_t* h) {
   if (!h) return fail(IBFEM_ERR_ARG, "null handle");
   if (h->opt.host_only) return fail(IBFEM_ERR_STATE, "handle was created host_only");
+  if (h->batch) return fail(IBFEM_ERR_STATE, "handle is a member of a batch (poll it out first)");
   cudaError_t e = cudaSetDevice(h->opt.device);
   if (e != cudaSuccess) return fail(IBFEM_ERR_CUDA, cudaGetErrorString(e));
   return IBFEM_OK;

@@ -48,6 +48,12 @@ struct Handle {
   cudaGraphExec_t graphs[2] = {nullptr, nullptr};
   std::vector<void*> allocs;
   size_t device_bytes = 0;
+  // K_ref image as uploaded (batched launches share equal images between members)
+  std::vector<uint16_t> tc_img_host;
+  std::vector<int> tc_frow_host;
+  void* batch = nullptr;   // the batch this handle is a member of (its steps run there)
+  // device bytes build_device allocates (sources, observers and the IMEX factor excluded)
+  size_t planned_device_bytes() const;
   bool have_dt = false, have_init = false;
   double dt = 0.0;
   int64_t step = 0, ring_start = 0;
@@ -76,6 +82,9 @@ struct Handle {
   void enqueue_step(int cur);
   void run_steps(int64_t n);
 };
+
+// Remove a member from its batch (batch.cu): waits for the batch's queued work first.
+void batch_forget(Handle* h);
 
 }  // namespace ibfem
 

@@ -102,6 +102,15 @@ def lib():
         "ibfem_get_element": (C.c_int, [vp, C.c_int64, DP, DP]),
         "ibfem_apply_operator_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
+        "ibfem_upload": (C.c_int, [vp]),
+        "ibfem_batch_create": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
+        "ibfem_batch_add": (C.c_int, [vp, vp, C.c_int64]),
+        "ibfem_batch_run": (C.c_int, [vp, C.c_int64]),
+        "ibfem_batch_poll": (C.c_int, [vp, C.POINTER(vp), C.c_int, C.POINTER(C.c_int)]),
+        "ibfem_batch_status": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+        "ibfem_batch_sync": (C.c_int, [vp]),
+        "ibfem_batch_wait": (C.c_int, [vp, C.c_int]),
+        "ibfem_batch_destroy": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -212,6 +221,10 @@ class Solver:
         self.close()
 
     # -- calls
+    def upload(self):
+        """Move a host-only handle onto its device (``ibfem_upload``)."""
+        _check(lib().ibfem_upload(self.h))
+
     def info(self):
         i = Info()
         _check(lib().ibfem_info(self.h, C.byref(i)))
@@ -294,6 +307,59 @@ class Solver:
         ml = np.zeros(self.n_loc)
         _check(lib().ibfem_get_element(self.h, int(cell), _dp(K), _dp(ml)))
         return K, ml
+
+
+class Batch:
+    """Continuous batching of exact tensor-core CDM solvers (``ibfem_batch_*``)."""
+
+    def __init__(self, stream=None, device=0):
+        b = C.c_void_p()
+        _check(lib().ibfem_batch_create(stream, device, C.byref(b)))
+        self.b = b
+        self._members = {}   # handle address -> Solver
+
+    def add(self, solver, n_steps):
+        _check(lib().ibfem_batch_add(self.b, solver.h, int(n_steps)))
+        self._members[solver.h.value] = solver
+
+    def run(self, n):
+        _check(lib().ibfem_batch_run(self.b, int(n)))
+
+    def poll(self, max_done=64):
+        """Solvers whose budget is used up (ordinary handles again)."""
+        arr = (C.c_void_p * max(int(max_done), 1))()
+        n = C.c_int()
+        _check(lib().ibfem_batch_poll(self.b, arr, int(max_done), C.byref(n)))
+        return [self._members.pop(arr[i]) for i in range(n.value)]
+
+    def status(self):
+        a, f, s = C.c_int(), C.c_int(), C.c_int64()
+        _check(lib().ibfem_batch_status(self.b, C.byref(a), C.byref(f), C.byref(s)))
+        return a.value, f.value, s.value
+
+    def wait(self, max_pending):
+        _check(lib().ibfem_batch_wait(self.b, int(max_pending)))
+
+    def sync(self):
+        _check(lib().ibfem_batch_sync(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().ibfem_batch_destroy(self.b)
+            self.b = None
+            self._members = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def apply_operator_noalloc(dim, p, ncomp, n_cells, cell_class, cut_index, cut_cells, n_cut,

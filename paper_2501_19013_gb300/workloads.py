@@ -220,6 +220,69 @@ def porous_voxel(n: int = 64, vn: int = 128, p: int = 3, seed: int = 0,
                     observers=obs)
 
 
+def _solid_point(rng: SplitMix64, dim: int, holes: Optional[np.ndarray], img: Optional[np.ndarray]) -> np.ndarray:
+    """A point in [0.1, 0.9]^dim outside every hole (2D) or moved to solid voxels (3D)."""
+    for _ in range(1000):
+        x = np.array([rng.uniform(0.1, 0.9) for _ in range(dim)])
+        if img is not None:
+            return nearest_solid_point(img, x)
+        if holes is None or all(np.sum((x - h[:dim]) ** 2) > (1.1 * h[dim]) ** 2 for h in holes):
+            return x
+    raise RuntimeError("no solid point found")
+
+
+def serving_request(seed: int) -> Workload:
+    """One request of the serving stream: a random 2D plate with holes (32^2 to 256^2 cells,
+    p = 2..4, scalar or plane strain) or a random 3D porous cube (16^3 to 48^3 cells,
+    p = 2..3, voxel image at 2 voxels per cell and axis), eigenvalue stabilisation, a
+    Ricker point source at a random solid position and 500 to 5000 steps."""
+    rng = SplitMix64(0x5EB1CE ^ (seed * 0x9E3779B97F4A7C15))
+
+    def pick(values, weights):
+        u, acc = rng.uniform(), 0.0
+        for v, w in zip(values, weights):
+            acc += w
+            if u < acc:
+                return v
+        return values[-1]
+
+    steps = 500 + int(rng.uniform() * 4501)
+    if rng.uniform() < 0.7:
+        n = pick([32, 64, 128, 256], [0.35, 0.3, 0.2, 0.15])
+        p = pick([2, 3, 4], [1 / 3, 1 / 3, 1 / 3])
+        physics = "elastic" if rng.uniform() < 0.3 else "scalar"
+        count = 1 + int(rng.uniform() * 12)
+        holes = random_holes(count, 0.02, 0.08, seed=int(rng.next_u64() & 0xFFFFFFFF))
+        xs = _solid_point(rng, 2, holes, None)
+        src = {"kind": "point", "x": list(xs)}
+        if physics == "elastic":
+            src["dir"] = [1.0, 0.0]
+        return Workload(name=f"serve_{seed}_2d_{n}_p{p}_{physics}", dim=2, n=(n, n), p=p,
+                        physics=physics, alpha=1e-5, quad_depth=3, holes=holes, stab="evs",
+                        eps=1e-4, f_lambda=1e-2, source=src, f0=10.0, steps=steps,
+                        observers=observers_outside_holes(default_observers(2), holes))
+    n = pick([16, 24, 32, 48], [0.4, 0.3, 0.2, 0.1])
+    p = pick([2, 3], [0.5, 0.5])
+    vn = 2 * n
+    img = random_void_image(vn, max(1.0, 4.0 * vn / 128.0), max(2.0, 12.0 * vn / 128.0),
+                            0.1 + 0.2 * rng.uniform(), int(rng.next_u64() & 0xFFFFFFFF))
+    xs = _solid_point(rng, 3, None, img)
+    obs = np.array([nearest_solid_point(img, x) for x in default_observers(3)])
+    return Workload(name=f"serve_{seed}_3d_{n}_p{p}", dim=3, n=(n, n, n), p=p, physics="scalar",
+                    alpha=1e-5, quad_depth=1, voxels=img, stab="evs", eps=1e-4, f_lambda=1e-2,
+                    source={"kind": "point", "x": list(xs)}, f0=10.0, steps=steps, observers=obs)
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: exponential gaps of mean 1 / rate."""
+    rng = SplitMix64(0xA5517A1 ^ seed)
+    t, out = 0.0, np.zeros(count)
+    for i in range(count):
+        t += -math.log(1.0 - rng.uniform()) / rate
+        out[i] = t
+    return out
+
+
 WORKLOADS = {
     "plate_one_hole": plate_one_hole,
     "plate_holes_elastic": plate_holes_elastic,
