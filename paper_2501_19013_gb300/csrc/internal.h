@@ -20,7 +20,7 @@ struct DevProblem {
   int n_cut;
   const double* Kref;       // n_loc^2 (symmetric)
   const double* Kcut;       // n_cut * n_loc^2 (symmetric, row-major)
-  const float* Kcut32;      // per cut cell: FP32 hi slice then lo slice (n_loc^2 each)
+  const float* Kcut32;      // per cut cell: n_loc^2 interleaved FP32 (hi, lo) pairs
   double* Ycut;             // n_cut * n_loc: K^e x_e of the cut cells for the current step
   const double* minv;       // dt^2 / M_L per lattice DOF (0 = dead); -(c + 1) marks IMEX c-DOF c
   const double* sinv;       // 1 / sqrt(M_L) per lattice DOF (0 = dead or IMEX c-DOF)
@@ -47,6 +47,7 @@ struct DevProblem {
   int tc_tiles[3];          // tile grid of the tensor-core kernel
   const uint16_t* tc_bimg;  // K_ref as UMMA B operand: four BF16 slices (digits or hi/lo)
   const int* tc_frow;       // exact scheme: unbiased exponent F_i of each K_ref row
+  const int32_t* tc_order;  // tensor-core tiles in processing order (costliest first), or null
   const float* minv32;      // dt^2 / M_L as two FP32 slices: hi[n_lat_dof] then lo[n_lat_dof]
   const int32_t* tsrc_ptr;  // source CSR over the tensor-core tile grid
   const int64_t* tsrc_dof;

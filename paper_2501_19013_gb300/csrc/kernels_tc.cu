@@ -213,7 +213,8 @@ struct TcCfg {
   static constexpr size_t OFF_B = OFF_A + A_BYTES;
   static constexpr size_t OFF_Y = Y_ALIAS ? 0 : OFF_B + B_BYTES;
   static constexpr size_t OFF_PATCH = ((Y_ALIAS ? OFF_B + B_BYTES : OFF_Y + Y_BYTES) + 15) / 16 * 16;
-  static constexpr size_t OFF_E = OFF_PATCH + 8 * (size_t)PATCH;           // int E[128]
+  static constexpr size_t PATCH_BYTES = (8 * (size_t)PATCH + 15) / 16 * 16;  // one patch buffer
+  static constexpr size_t OFF_E = OFF_PATCH + 2 * PATCH_BYTES;              // int E[128]
   static constexpr size_t OFF_F = OFF_E + 4 * (4 + 128 + 8);                 // int F[NP]
   static constexpr size_t OFF_OFF = OFF_F + 4 * (size_t)NP;                  // int off[KP]
   static constexpr size_t OFF_XS = (OFF_OFF + 4 * (size_t)KP + 15) / 16 * 16;  // 8 warps x 2 x NL floats
@@ -238,7 +239,7 @@ __host__ __device__ __forceinline__ int bf16_core_offset(int row, int k) {
 // CTA keeps the descriptor of its current member in shared memory and reloads the K_ref
 // image only when a member with another image comes up (the host orders members by image).
 template <int DIM, int P, int NC, int SCHEME, bool BATCH>
-__global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevProblem pb_arg, const double* u_arg,
+__global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ DevProblem pb_arg, const double* u_arg,
                                                     double* out_arg, int mode,
                                                     const BatchMember* __restrict__ members,
                                                     const int* __restrict__ tile_start, int n_members,
@@ -250,10 +251,13 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
   extern __shared__ __align__(1024) unsigned char smem[];
   uint16_t* A = reinterpret_cast<uint16_t*>(smem + C::OFF_A);
   uint16_t* B = reinterpret_cast<uint16_t*>(smem + C::OFF_B);
-  float* yD = reinterpret_cast<float*>(smem + C::OFF_Y);      // level 0, scaled to its value
-  float* yL = yD + C::NE * NL;                                // levels 1-3, scaled
-  double* patch = reinterpret_cast<double*>(smem + C::OFF_PATCH);
-  uint2* dpatch = reinterpret_cast<uint2*>(patch);            // the same storage as 4 BF16 digits
+  // per (cell, row): level 0 and the combined levels 1-3, both scaled to their value
+  float2* yb = reinterpret_cast<float2*>(smem + C::OFF_Y);
+  // two patch buffers, swapped every tile: the FP64 node patch of u^k (read by the digit
+  // conversion, the cut cells and the update) and the BF16 digits of it (read by the A
+  // gather), which then receives the next tile's FP64 patch
+  auto pbuf = [&](int which) { return reinterpret_cast<double*>(smem + C::OFF_PATCH + which * C::PATCH_BYTES); };
+  int pcur = 0;
   int* Eb = reinterpret_cast<int*>(smem + C::OFF_E);          // Eb[0]: tile exponent; Eb[1..]: lists
   int* Fr = reinterpret_cast<int*>(smem + C::OFF_F);
   int* off = reinterpret_cast<int*>(smem + C::OFF_OFF);
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
   int* special = Eb + 4;                                      // cut / outside cells of the tile
   int* wmax = Eb + 4 + 128;                                   // per-warp exponent maxima
   int* next_member = n_special + 1;                           // batched: member of next_tile
+  int* next_local = n_special + 2;                            // next_tile within its problem, ordered
   BatchMember* sbm = reinterpret_cast<BatchMember*>(smem + C::SMEM);  // batched: current member
   const DevProblem& pb = BATCH ? sbm->pb : pb_arg;
   const double* __restrict__ u = u_arg;
@@ -283,6 +288,36 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
     }
     return lo;
   };
+
+  // asynchronous load of the node patch of `tile` (zero outside the lattice)
+  auto issue_patch = [&](int t, double* patch) {
+    const int ibx = t % pb.tc_tiles[0];
+    const int iby = (t / pb.tc_tiles[0]) % pb.tc_tiles[1];
+    const int ibz = DIM == 3 ? t / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
+    const int hx0 = (ibx * C::TX - 1) * P, hy0 = (iby * C::TY - 1) * P;
+    const int hz0 = DIM == 3 ? (ibz * C::TZ - 1) * P : 0;
+    for (int node = tid; node < NV / NC; node += blockDim.x) {
+      int px = node % PX, py = (node / PX) % PY, pz = node / (PX * PY);
+      int gx = hx0 + px, gy = hy0 + py, gz = hz0 + pz;
+      bool in = gx >= 0 && gx < pb.lat[0] && gy >= 0 && gy < pb.lat[1] && gz >= 0 && gz < pb.lat[2];
+      int64_t g = in ? (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC : 0;
+      cp_async_zfill<8 * NC>(patch + node * NC, u + g, in ? 8 * NC : 0);
+    }
+  };
+
+  // class of halo cell m of local tile t (0 outside the domain)
+  auto halo_class = [&](int t, int m) -> int {
+    const int tbx = t % pb.tc_tiles[0];
+    const int tby = (t / pb.tc_tiles[0]) % pb.tc_tiles[1];
+    const int tbz = DIM == 3 ? t / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
+    const int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
+    const int ex = tbx * C::TX - 1 + elx, ey = tby * C::TY - 1 + ely, ez = DIM == 3 ? tbz * C::TZ - 1 + elz : 0;
+    const bool in_dom =
+        ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
+    return in_dom ? (int)pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
+  };
+  int my_cl = 0;   // class of halo cell `tid` of the prefetched tile (valid with have_patch)
+  bool have_patch = false;   // the current tile's patch was loaded ahead
 
   // ---- once per CTA: TMEM, barriers, K_ref digits (bulk copy), tables, observers
   if (warp == 0) {
@@ -304,10 +339,32 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
                  "l"(pb.tc_bimg), "r"(bytes), "r"(smem_u32(&bars[0]))
                  : "memory");
   }
+  // global tile g -> (member, tile of that member in processing order); thread 0 only
+  auto resolve = [&](int g, int& m, int& t) {
+    m = 0;
+    t = 0;
+    if (g >= n_tiles) return;
+    if (BATCH) m = member_of(g);
+    const int local = BATCH ? g - tile_start[m] : g;
+    const int32_t* ord = BATCH ? members[m].pb.tc_order : pb_arg.tc_order;
+    t = ord ? ord[local] : local;
+  };
+  // single problem: CTA b starts with global tile b (the counter hands out the rest), whose
+  // patch load is issued right away and overlaps the set-up below
+  if (!BATCH) {
+    const int t0 = pb_arg.tc_order ? pb_arg.tc_order[blockIdx.x] : (int)blockIdx.x;
+    issue_patch(t0, pbuf(0));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    have_patch = true;
+    if (tid < C::NE) my_cl = halo_class(t0, tid);
+  }
   if (tid == 0) {
-    const int g = atomicAdd(tcount, 1);
+    const int g = BATCH ? atomicAdd(tcount, 1) : (int)blockIdx.x;
+    int m, t;
+    resolve(g, m, t);
     *next_tile = g;
-    if (BATCH) *next_member = g < n_tiles ? member_of(g) : 0;
+    *next_member = m;
+    *next_local = t;
   }
   if (!BATCH)
     for (int i = tid; i < NP; i += blockDim.x) Fr[i] = pb.tc_frow ? pb.tc_frow[i] : 0;
@@ -337,7 +394,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
                          ((uint32_t)(128 >> 4) << 24);
   const uint32_t aS[2] = {smem_u32(A), smem_u32(A + C::A_SLICE)};
   const uint32_t bS0 = smem_u32(B);
-  bool ok = true, bimg_ready = false, bad = false, have_patch = false;
+  bool ok = true, bimg_ready = false, bad = false;
   int cur_m = -1;                       // batched: member whose descriptor is in shared memory
   const uint16_t* cur_bimg = nullptr;   // batched: K_ref image in shared memory
   uint32_t b_loads = BATCH ? 0u : 1u;   // K_ref image loads issued (phase of bars[0])
@@ -347,26 +404,11 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
   constexpr int ITEMS = ROWS * KG;
   constexpr int IPT = (ITEMS + 255) / 256;
 
-  // asynchronous load of the node patch of `tile` (zero outside the lattice)
-  auto issue_patch = [&](int t) {
-    const int ibx = t % pb.tc_tiles[0];
-    const int iby = (t / pb.tc_tiles[0]) % pb.tc_tiles[1];
-    const int ibz = DIM == 3 ? t / (pb.tc_tiles[0] * pb.tc_tiles[1]) : 0;
-    const int hx0 = (ibx * C::TX - 1) * P, hy0 = (iby * C::TY - 1) * P;
-    const int hz0 = DIM == 3 ? (ibz * C::TZ - 1) * P : 0;
-    for (int node = tid; node < NV / NC; node += blockDim.x) {
-      int px = node % PX, py = (node / PX) % PY, pz = node / (PX * PY);
-      int gx = hx0 + px, gy = hy0 + py, gz = hz0 + pz;
-      bool in = gx >= 0 && gx < pb.lat[0] && gy >= 0 && gy < pb.lat[1] && gz >= 0 && gz < pb.lat[2];
-      int64_t g = in ? (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC : 0;
-      cp_async_zfill<8 * NC>(patch + node * NC, u + g, in ? 8 * NC : 0);
-    }
-  };
 
   for (;;) {
     const int gt = *next_tile;
     if (gt >= n_tiles) break;
-    int tile = gt;
+    const int tile = *next_local;   // this problem's tile, in processing order
     bool skip = false;
     if constexpr (BATCH) {
       const int m = *next_member;
@@ -399,7 +441,6 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
         cur_m = m;
         have_patch = false;
       }
-      tile = gt - tile_start[m];
       skip = k >= sbm->step_end;
     }
     const uint32_t par = mma_phase & 1u;
@@ -411,20 +452,33 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
     const int Z1 = DIM == 3 ? min(Z0 + C::TZ, pb.n[2]) : 1;
 
     // ---- node patch of u^k: prefetched during the previous tile's update, else loaded now
+    double* const pf = pbuf(pcur);                                  // FP64 patch of u^k
+    uint2* const dpd = reinterpret_cast<uint2*>(pbuf(pcur ^ 1));    // its digits
     if (!have_patch && !skip) {
-      issue_patch(tile);
+      issue_patch(tile, pf);
       cp_async_commit_wait_all();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // a patch loaded ahead has landed
     // cut / outside cells of the halo'd tile (class byte per cell, compact list)
     if (tid == 0) *n_special = 0;
     __syncthreads();
-    if (tid == 0) {   // read after the loop-end barrier
-      const int g = atomicAdd(tcount, 1);
-      *next_tile = g;
-      if (BATCH) *next_member = g < n_tiles ? member_of(g) : 0;
-    }
+    // the next tile: the atomic's latency is hidden behind this tile's work; thread 0
+    // publishes the result before the drain barrier (it is read after that barrier)
+    // (its lookups are resolved after the digit conversion, published before the drain
+    // barrier and read after it)
+    int g_next = 0, m_next = 0, t_next = 0;
+    if (tid == 0) g_next = atomicAdd(tcount, 1) + (BATCH ? 0 : (int)gridDim.x);
+    auto publish_next = [&]() {
+      if (tid == 0) {
+        *next_tile = g_next;
+        *next_member = m_next;
+        *next_local = t_next;
+      }
+    };
     if (skip) {   // batched: this member has taken all its steps
       have_patch = false;
+      if (tid == 0) resolve(g_next, m_next, t_next);
+      publish_next();
       __syncthreads();
       continue;
     }
@@ -437,12 +491,8 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
       }
     }
     if (tid < C::NE) {
-      int m = tid;
-      int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-      int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
-      bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
-      uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
-      if (cl != 2) special[atomicAdd(n_special, 1)] = m;
+      const int cl = have_patch ? my_cl : halo_class(tile, tid);
+      if (cl != 2) special[atomicAdd(n_special, 1)] = tid | (cl << 8);
     }
 
     // ---- tile exponent (largest biased FP64 exponent of the patch), then the patch is
@@ -450,7 +500,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
     int em = 0;
     if (SCHEME == 0) {
       int e = 0;
-      for (int i = tid; i < NV; i += blockDim.x) e = max(e, (int)((__double_as_longlong(patch[i]) >> 52) & 0x7ff));
+      for (int i = tid; i < NV; i += blockDim.x) e = max(e, (int)((__double_as_longlong(pf[i]) >> 52) & 0x7ff));
       e = __reduce_max_sync(0xffffffffu, e);
       if (lane == 0) wmax[warp] = e;
       __syncthreads();
@@ -459,7 +509,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
       for (int w = 1; w < 8; ++w) em = max(em, wmax[w]);
     }
     for (int i = tid; i < NV; i += blockDim.x) {
-      double x = patch[i];
+      double x = pf[i];
       uint32_t lo16, hi16;
       if (SCHEME == 0) {
         int dg[4];
@@ -472,10 +522,11 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
         lo16 = h | ((uint32_t)bf16_rn(xf - __uint_as_float((uint32_t)h << 16)) << 16);
         hi16 = 0;
       }
-      dpatch[i] = make_uint2(lo16, hi16);
+      dpd[i] = make_uint2(lo16, hi16);
     }
     __syncthreads();
 
+    if (tid == 0) resolve(g_next, m_next, t_next);   // the atomic has long returned
     // ---- A operand: each item writes one 8-element row of a core matrix (16 bytes) of slots
     // 0 and 1 by copying digits; slices 2 and 3 stay in registers until phase 2
     uint32_t keep[IPT][8];
@@ -489,7 +540,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
       uint32_t w[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
       if (m < C::NE && kg * 8 < NL) {
         int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
-        const uint2* xe = dpatch + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
+        const uint2* xe = dpd + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
 #pragma unroll
         for (int q = 0; q < 8; q += 2) {
           const int j = kg * 8 + q;
@@ -581,14 +632,16 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ready) {
       if (tid == 0) atomicOr(pb.flags, 2);
-    } else if (warp < 4) {
-      // ---- drain TMEM: level 0 and the combined levels 1-3, both scaled to their value
-      // 2^(E + F_i - 14) by exponent arithmetic (exact; the exponent is the tile's)
-      const int m = warp * 32 + lane;
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    } else {
+      // ---- drain TMEM: level 0 and the combined levels 1-3, both scaled to their value by
+      // a multiplication with 2^(E + F_i - 14) (exact: D0 is an integer below 2^24; values
+      // below the FP32 normal range are negligible).  Warps w and w + 4 share the lane
+      // quarter w % 4 and split the column blocks.
+      const int m = (warp & 3) * 32 + lane;
+      const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
       const int ebase = em - 1023 - 14;
 #pragma unroll 1
-      for (int c0 = 0; c0 < NP; c0 += 16) {
+      for (int c0 = (warp >> 2) * 16; c0 < NP; c0 += 32) {
         uint32_t r[4][16];
 #pragma unroll
         for (int l = 0; l < (SCHEME == 0 ? 4 : 1); ++l) {
@@ -608,82 +661,93 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
             if (i < NL) {
               if (SCHEME == 0) {
                 const int sh = ebase + Fr[i];
+                const float sc = sh < -126 ? 0.f : __int_as_float((min(sh, 127) + 127) << 23);
                 float lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
                                 fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f,
                                      __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
-                yD[m * NL + i] = f32_scale(__uint_as_float(r[0][q]), sh);
-                yL[m * NL + i] = f32_scale(lo, sh);
+                yb[m * NL + i] = make_float2(__uint_as_float(r[0][q]) * sc, lo * sc);
               } else {
-                yD[m * NL + i] = __uint_as_float(r[0][q]);
-                yL[m * NL + i] = 0.f;
+                yb[m * NL + i] = make_float2(__uint_as_float(r[0][q]), 0.f);
               }
             }
           }
         }
       }
     }
+    publish_next();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+
+    // ---- the digit buffer is free: the next tile's FP64 patch goes there (asynchronously,
+    // landing during the cut cells and the update)
+    {
+      const int nt = *next_tile;
+      have_patch = nt < n_tiles && (!BATCH || *next_member == cur_m);
+      if (have_patch) {
+        const int lt = *next_local;
+        issue_patch(lt, pbuf(pcur ^ 1));
+        if (tid < C::NE) my_cl = halo_class(lt, tid);   // consumed at the next tile's top
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
 
     // ---- cut and outside cells replace their rows (double-FP32 on the CUDA cores; u^k from
     // global memory, the patch now holds digits)
     const int nsp = *n_special;
     for (int q = warp; q < nsp; q += 8) {
-      const int m = special[q];
+      const int m = special[q] & 0xff, cl = special[q] >> 8;
       int elx = m % EX, ely = (m / EX) % EY, elz = m / (EX * EY);
       int ex = X0 - 1 + elx, ey = Y0 - 1 + ely, ez = DIM == 3 ? Z0 - 1 + elz : 0;
-      bool in_dom = ex >= 0 && ex < pb.n[0] && ey >= 0 && ey < pb.n[1] && (DIM == 2 || (ez >= 0 && ez < pb.n[2]));
-      uint8_t cl = in_dom ? pb.cls[((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex] : 0;
       if (cl == 0) {
-        for (int i = lane; i < NL; i += 32) {
-          yD[m * NL + i] = 0.f;
-          yL[m * NL + i] = 0.f;
-        }
+        for (int i = lane; i < NL; i += 32) yb[m * NL + i] = make_float2(0.f, 0.f);
         continue;
       }
       float* xh = xs + warp * 2 * NL;
       float* xl = xh + NL;
+      const double* xe = pf + ((elz * P * PY + ely * P) * PX + elx * P) * NC;
       for (int j = lane; j < NL; j += 32) {
-        int node = j / NC, comp = j % NC;
-        int a = node % NN1, b = (node / NN1) % NN1, c = DIM == 3 ? node / (NN1 * NN1) : 0;
-        int64_t g = ((((int64_t)(ez * P + c) * pb.lat[1]) + (ey * P + b)) * pb.lat[0] + ex * P + a) * NC + comp;
-        double x = u[g];
+        const double x = xe[off[j]];
         float h = f64_to_f32_rn(x);
         xh[j] = h;
         xl[j] = f64_to_f32_rn(x - f32_to_f64_scaled(h, 0));
       }
       __syncwarp();
       const int64_t cell = ((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex;
-      const float* Kh = pb.Kcut32 + (size_t)pb.cut_index[cell] * 2 * NL * NL;
-      const float* Kl = Kh + NL * NL;
-      for (int i = lane; i < NL; i += 32) {
-        float sacc = 0.f, c = 0.f;
-        for (int j = 0; j < NL; ++j) {
-          float kh = Kh[(size_t)j * NL + i], kl = Kl[(size_t)j * NL + i];
-          float p = kh * xh[j];
-          float pe = fmaf(kh, xh[j], -p);          // exact error of the product
-          pe = fmaf(kh, xl[j], fmaf(kl, xh[j], pe));
+      // K^e as (hi, lo) FP32 pairs, column j contiguous over the rows i; the lane's rows
+      // run as independent chains and the loads of several columns are in flight together
+      const float2* K2 = reinterpret_cast<const float2*>(pb.Kcut32) + (size_t)pb.cut_index[cell] * NL * NL;
+      constexpr int R = (NL + 31) / 32;
+      float sacc[R], cacc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) sacc[r] = cacc[r] = 0.f;
+#pragma unroll 10
+      for (int j = 0; j < NL; ++j) {
+        const float xhj = xh[j], xlj = xl[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          // rows past NL (last chain of some lanes) compute on row NL - 1 and are dropped
+          const float2 kk = __ldg(K2 + (size_t)j * NL + min(lane + 32 * r, NL - 1));
+          const float p = kk.x * xhj;
+          float pe = fmaf(kk.x, xhj, -p);          // exact error of the product
+          pe = fmaf(kk.x, xlj, fmaf(kk.y, xhj, pe));
           float t, e;
-          two_sum(sacc, p, t, e);
-          sacc = t;
-          c += e + pe;
+          two_sum(sacc[r], p, t, e);
+          sacc[r] = t;
+          cacc[r] += e + pe;
         }
-        float hs, he;
-        two_sum(sacc, c, hs, he);
-        yD[m * NL + i] = hs;
-        yL[m * NL + i] = he;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i < NL) {
+          float hs, he;
+          two_sum(sacc[r], cacc[r], hs, he);
+          yb[m * NL + i] = make_float2(hs, he);
+        }
       }
       __syncwarp();
     }
     __syncthreads();
-    // the patch is free from here on: start loading the next tile's (tile index is known)
-    {
-      const int nt = *next_tile;
-      have_patch = nt < n_tiles && (!BATCH || *next_member == cur_m);
-      if (have_patch) issue_patch(BATCH ? nt - tile_start[cur_m] : nt);
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-
     // ---- node-centric assembly and the FP64 update (owned nodes, no runtime division)
     const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
     const int nox = (X1 - X0) * P + (X1 == pb.n[0] ? 1 : 0);
@@ -696,67 +760,76 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
       src_hi = pb.tsrc_ptr[tile + 1];
     }
     constexpr int TOTAL = WX * WY * WZ * NC;
-    constexpr int NB = 3;   // items per thread and round: their global loads are issued together
+    // every global load of a thread's items is issued before any of them is used (one
+    // memory round trip per tile instead of one per few items)
+    constexpr int NB = (TOTAL + 255) / 256 < 5 ? (TOTAL + 255) / 256 : 5;
+    auto decode = [&](int i, int& comp, int& lx, int& ly, int& lz) {
+      comp = i % NC;
+      const int node = i / NC;
+      lx = node % WX;
+      ly = (node / WX) % WY;
+      lz = node / (WX * WY);
+    };
     for (int base = tid; base < TOTAL; base += NB * 256) {
-      int64_t dofs[NB];
-      int locs[NB];
-      bool act[NB];
       double upv[NB], ukv[NB];
       float mhv[NB], mlv[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const int i = base + b * 256;
-        const int comp = i % NC, node = i / NC;
-        const int lx = node % WX, ly = (node / WX) % WY, lz = node / (WX * WY);
-        act[b] = i < TOTAL && lx < nox && ly < noy && lz < noz;
-        const int gx = ox0 + lx, gy = oy0 + ly, gz = oz0 + lz;
-        dofs[b] = (((int64_t)gz * pb.lat[1] + gy) * pb.lat[0] + gx) * NC + comp;
-        locs[b] = i;
+        int comp, lx, ly, lz;
+        decode(i, comp, lx, ly, lz);
+        const bool act = i < TOTAL && lx < nox && ly < noy && lz < noz;
+        const int64_t dof = (((int64_t)(oz0 + lz) * pb.lat[1] + (oy0 + ly)) * pb.lat[0] + (ox0 + lx)) * NC + comp;
         upv[b] = 0.0;
         ukv[b] = 0.0;
         mhv[b] = 0.f;
         mlv[b] = 0.f;
-        if (act[b] && mode != kModeApply) {
-          mhv[b] = __ldg(pb.minv32 + dofs[b]);
-          mlv[b] = __ldg(pb.minv32 + pb.n_lat_dof + dofs[b]);
-          upv[b] = out[dofs[b]];
-          ukv[b] = __ldg(u + dofs[b]);   // L2-resident: the patch buffer now holds the next tile
+        if (act && mode != kModeApply) {
+          mhv[b] = __ldg(pb.minv32 + dof);
+          mlv[b] = __ldg(pb.minv32 + pb.n_lat_dof + dof);
+          upv[b] = out[dof];
+          ukv[b] = pf[(((DIM == 3 ? lz + P : 0) * PY + (ly + P)) * PX + (lx + P)) * NC + comp];
         }
       }
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        if (!act[b]) continue;
-        const int comp = locs[b] % NC, node = locs[b] / NC;
-        const int lx = node % WX, ly = (node / WX) % WY, lz = node / (WX * WY);
+        const int i = base + b * 256;
+        int comp, lx, ly, lz;
+        decode(i, comp, lx, ly, lz);
+        if (!(i < TOTAL && lx < nox && ly < noy && lz < noz)) continue;
+        const int64_t dof = (((int64_t)(oz0 + lz) * pb.lat[1] + (oy0 + ly)) * pb.lat[0] + (ox0 + lx)) * NC + comp;
+        // the (up to 2^DIM) cells of the halo'd tile that hold this node, in a fixed order;
+        // level-0 parts summed error-free in FP32 (s + e is their exact sum)
         const int px = lx + P, py = ly + P, pz = DIM == 3 ? lz + P : 0;
         const int cx = px / P, cy = py / P, cz = DIM == 3 ? pz / P : 0;
-        const int nxe = (px % P == 0) ? 2 : 1, nye = (py % P == 0) ? 2 : 1;
-        const int nze = DIM == 3 ? ((pz % P == 0) ? 2 : 1) : 1;
-        double hi = 0.0;
-        float lo = 0.f;
-        bool first = true;
-        for (int iz = 0; iz < nze; ++iz)
-          for (int iy = 0; iy < nye; ++iy)
-            for (int ix = 0; ix < nxe; ++ix) {
-              const int ecx = cx - (nxe - 1) + ix, ecy = cy - (nye - 1) + iy, ecz = DIM == 3 ? cz - (nze - 1) + iz : 0;
-              if (ecx >= EX || ecy >= EY || (DIM == 3 && ecz >= C::EZ)) continue;
-              const int m = (ecz * EY + ecy) * EX + ecx;
-              const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
-              double v = f32_to_f64_scaled(yD[m * NL + row], 0);
-              hi = first ? v : hi + v;
-              first = false;
-              lo += yL[m * NL + row];
+        const bool bx = px - cx * P == 0, by = py - cy * P == 0, bz = DIM == 3 && pz - cz * P == 0;
+        float sh = 0.f, se = 0.f, lo = 0.f;
+#pragma unroll
+        for (int jz = 0; jz < (DIM == 3 ? 2 : 1); ++jz)
+#pragma unroll
+          for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+            for (int jx = 0; jx < 2; ++jx) {
+              const int ecx = cx - 1 + jx, ecy = cy - 1 + jy, ecz = DIM == 3 ? cz - 1 + jz : 0;
+              const bool val = (jx ? cx < EX : bx) && (jy ? cy < EY : by) &&
+                               (DIM == 2 || (jz ? cz < C::EZ : bz));
+              if (val) {
+                const int m = (ecz * EY + ecy) * EX + ecx;
+                const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
+                const float2 y = yb[m * NL + row];
+                float t1, t2;
+                two_sum(sh, y.x, t1, t2);
+                sh = t1;
+                se += t2;
+                lo += y.y;
+              }
             }
-        const int64_t dof = dofs[b];
         if (mode == kModeApply) {
-          out[dof] = hi + f32_to_f64_scaled(lo, 0);
+          out[dof] = f32_to_f64_scaled(sh, 0) + f32_to_f64_scaled(se + lo, 0);
           continue;
         }
         if (!(mhv[b] > 0.f)) continue;
-        double t = -hi;
-        for (int s2 = src_lo; s2 < src_hi; ++s2)
-          if (pb.tsrc_dof[s2] == dof) t += pb.tsrc_val[s2] * fk;
-        const float r = f64_to_f32_rn(t) - lo;
+        const float r = -(sh + (se + lo));   // -K u rounded once to FP32 (the load follows below)
         const float d32 = fmaf(mhv[b], r, mlv[b] * r);
         if (!isfinite(d32)) bad = true;
         const double delta = f32_to_f64_scaled(d32, 0);
@@ -767,6 +840,17 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
           out[dof] = uval - pb.dt * upv[b] + 0.5 * delta;
       }
     }
+    // the load F_k of this tile's DOFs (each DOF once per tile), added after the update in
+    // FP64: u^{k+1} += (dt^2 / m) F_k (start-up step: half of it)
+    if (src_lo < src_hi && mode != kModeApply) {
+      __syncthreads();   // this tile's updates of `out` are visible to every thread
+      const double w = mode == kModeCDM ? 1.0 : 0.5;
+      for (int s2 = src_lo + tid; s2 < src_hi; s2 += blockDim.x) {
+        const int64_t dof = pb.tsrc_dof[s2];
+        const double mi = pb.minv[dof];
+        if (mi > 0.0) out[dof] = fma(w * mi, pb.tsrc_val[s2] * fk, out[dof]);
+      }
+    }
     if (BATCH && bad) {
       atomicOr(pb.flags, 1);
       bad = false;
@@ -774,6 +858,7 @@ __global__ void __launch_bounds__(256) op_tc_kernel(const __grid_constant__ DevP
     ++mma_phase;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();   // patch (prefetched), lists, A/ybuf and next_tile are reused by the next tile
+    if (have_patch) pcur ^= 1;
   }
   if (!BATCH && bad) atomicOr(pb.flags, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -209,14 +209,15 @@ void Handle::build_device() {
     pb.tc_frow = upload(frow);
     tc_img_host = img;
     tc_frow_host = frow;
+    // cut matrices as interleaved (hi, lo) FP32 pairs: one 8-byte load per entry
     std::vector<float> k32(2 * (size_t)s.n_cut * s.n_loc * s.n_loc);
     const size_t nl2 = (size_t)s.n_loc * s.n_loc;
     for (int64_t c = 0; c < s.n_cut; ++c)
       for (size_t q = 0; q < nl2; ++q) {
         double v = s.Kcut[c * nl2 + q];
         float h = (float)v;
-        k32[(2 * c) * nl2 + q] = h;
-        k32[(2 * c + 1) * nl2 + q] = (float)(v - (double)h);
+        k32[2 * (c * nl2 + q)] = h;
+        k32[2 * (c * nl2 + q) + 1] = (float)(v - (double)h);
       }
     pb.Kcut32 = upload(k32);
     std::vector<float> m32(2 * (size_t)s.n_lat_dof, 0.f);
@@ -231,6 +232,26 @@ void Handle::build_device() {
     pb.minv32 = d_minv32;
     op_tc_tiles(s.dim, s.p, s.ncomp, tc_tile);
     for (int k = 0; k < 3; ++k) pb.tc_tiles[k] = k < s.dim ? (s.n[k] + tc_tile[k] - 1) / tc_tile[k] : 1;
+    // processing order of the tiles: the persistent kernel hands tiles out in this order,
+    // so the slow ones (cut cells of the halo'd tile run on the CUDA cores, one warp per
+    // cell, eight at a time) start first and short tiles fill the end of the step
+    const int ntx = pb.tc_tiles[0], nty = pb.tc_tiles[1], ntz = pb.tc_tiles[2];
+    std::vector<int> ncut_tile((size_t)ntx * nty * ntz, 0);
+    for (int t = 0; t < ntx * nty * ntz; ++t) {
+      const int bx = t % ntx, by = (t / ntx) % nty, bz = t / (ntx * nty);
+      int c = 0;
+      for (int ez = (s.dim == 3 ? bz * tc_tile[2] - 1 : 0); ez < (s.dim == 3 ? (bz + 1) * tc_tile[2] : 1); ++ez)
+        for (int ey = by * tc_tile[1] - 1; ey < (by + 1) * tc_tile[1]; ++ey)
+          for (int ex = bx * tc_tile[0] - 1; ex < (bx + 1) * tc_tile[0]; ++ex) {
+            if (ex < 0 || ey < 0 || ez < 0 || ex >= s.n[0] || ey >= s.n[1] || (s.dim == 3 && ez >= s.n[2])) continue;
+            if (s.cls[((int64_t)ez * s.n[1] + ey) * s.n[0] + ex] == kCut) ++c;
+          }
+      ncut_tile[t] = (c + 7) / 8;   // rounds of eight warps
+    }
+    std::vector<int32_t> order(ncut_tile.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = (int32_t)t;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return ncut_tile[a] > ncut_tile[b]; });
+    pb.tc_order = upload(order);
   }
   scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
   lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
@@ -264,6 +285,11 @@ size_t Handle::planned_device_bytes() const {
     int kp = 0, np = 0;
     op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
     b += 4 * (size_t)kp * np * 2 + arr(np, 4);            // K_ref image, row exponents
+    int tt[3] = {1, 1, 1};
+    op_tc_tiles(s.dim, s.p, s.ncomp, tt);
+    int64_t ntc = 1;
+    for (int k = 0; k < s.dim; ++k) ntc *= (s.n[k] + tt[k] - 1) / tt[k];
+    b += arr(ntc, 4);                                     // tile order
     b += arr(2 * ncut * nl * nl, 4) + arr(2 * nlat, 4);   // Kcut32, minv32
   }
   b += 64 + kPowerChunk * 8 + arr(nlat, 8);               // scalars, lam_hist, scratch
