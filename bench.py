@@ -318,8 +318,8 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic": f"2 n_loc^2 per uncut cell + 6 per DOF = {flops:.3e} flop"}
     else:
         # read u^k, u^{k-1} (FP64) and dt^2/m (two FP32 slices), write u^{k+1} (FP64): 32 B
-        # per DOF; the cut matrices as FP32 (hi, lo) pairs: 8 n_loc^2 B per cut cell
-        byts = 32.0 * n_dof + 8.0 * inf.n_cut * n_loc * n_loc
+        # per DOF; the cut matrices as FP32 (hi, lo) pairs: 8 n_loc^2 B per distinct matrix
+        byts = 32.0 * n_dof + 8.0 * inf.n_cut_matrices * n_loc * n_loc
         achieved = byts / (kms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         fp64_ops = 2.0 * n_dof          # fma(2, u, -u_prev) and + delta per DOF
@@ -328,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one cold launch of this kernel on this workload" if traffic else None,
-                "algorithmic": f"32 B/DOF + 8 n_loc^2 B per cut cell = {byts:.3e} B",
+                "algorithmic": f"32 B/DOF + 8 n_loc^2 B per distinct cut matrix ({inf.n_cut_matrices}) = {byts:.3e} B",
                 "fp64_alu_frac": fp64_ops / (kms * 1e-3) / (FP64_PEAK_GFLOPS * 1e9 / 2.0)}
 
     # end to end through the C ABI with host buffers
@@ -374,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
                        "stab": f"{rb['stab']} eps={w.eps:g} f_lambda={w.f_lambda:g} alpha={w.alpha:g}",
                        "scheme": rb["scheme"],
                        "n_dof": n_dof, "n_uncut": inf.n_uncut, "n_cut": inf.n_cut,
+                       "n_cut_matrices": inf.n_cut_matrices,
                        "precision": best, "state": "fp64", "dt": dt,
                        "l2": "flushed: 256 MiB device write before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -128,6 +128,9 @@ typedef struct {
     double lambda_ref;        /* lambda_max(K_ref, M_ref) of one uncut cell            */
     size_t device_bytes;      /* device memory held by the handle; for a host_only
                                  handle the bytes ibfem_upload would allocate            */
+    int64_t n_cut_matrices;   /* distinct cut-cell matrix sets: equal to n_cut, or fewer
+                                 for voxel images with whole voxels per cell, where cut
+                                 cells with equal voxel blocks share one set             */
 } ibfem_info_t;
 
 /* ---- lifetime -------------------------------------------------------------------- */

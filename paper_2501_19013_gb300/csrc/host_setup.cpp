@@ -21,6 +21,7 @@
 #include <functional>
 #include <stdexcept>
 #include <thread>
+#include <unordered_map>
 
 namespace ibfem {
 
@@ -723,14 +724,59 @@ Setup build_setup(const SetupInput& in) {
   s.lambda_ref = lambda_max_lumped(s.Kref.data(), s.mref.data());
   double mfull_max = *std::max_element(Mfull.begin(), Mfull.end());
 
-  // cut cells
-  s.Kcut.assign((size_t)s.n_cut * nl * nl, 0.0);
-  s.mlcut.assign((size_t)s.n_cut * nl, 0.0);
-  if (in.need_consistent_mass) s.Mcut.assign((size_t)s.n_cut * nl * nl, 0.0);
-  parallel_for(s.n_cut, [&](int64_t a, int64_t b) {
+  // distinct cut cells: with a voxel image holding a whole number r_k of voxels per cell and
+  // axis (prod r_k <= 64), a cut cell's integrals depend only on its voxel block, so cells
+  // with equal blocks share one set of matrices (computed for the first of them)
+  std::vector<int64_t> rep;   // matrix index -> representative cut index
+  s.cut_mat.assign(s.n_cut, 0);
+  {
+    const GeometryDesc& g = in.geom;
+    bool blocks = g.kind == 2;
+    int r[3] = {1, 1, 1}, nb = 1;
+    for (int k = 0; blocks && k < s.dim; ++k) {
+      blocks = g.vn[k] % s.n[k] == 0;
+      r[k] = blocks ? g.vn[k] / s.n[k] : 1;
+      nb *= r[k];
+    }
+    blocks = blocks && nb <= 64;
+    std::unordered_map<uint64_t, int32_t> seen;
+    for (int64_t ci = 0; ci < s.n_cut; ++ci) {
+      if (!blocks) {
+        s.cut_mat[ci] = (int32_t)rep.size();
+        rep.push_back(ci);
+        continue;
+      }
+      int64_t e = s.cut_cells[ci], rem = e, ic[3] = {0, 0, 0};
+      for (int k = 0; k < s.dim; ++k) {
+        ic[k] = rem % s.n[k];
+        rem /= s.n[k];
+      }
+      uint64_t key = 0;
+      int bit = 0;
+      for (int c = 0; c < (s.dim == 3 ? r[2] : 1); ++c)
+        for (int b = 0; b < r[1]; ++b)
+          for (int a = 0; a < r[0]; ++a, ++bit) {
+            int64_t vx = ic[0] * r[0] + a, vy = ic[1] * r[1] + b, vz = s.dim == 3 ? ic[2] * r[2] + c : 0;
+            if (g.voxels[(size_t)((vz * g.vn[1] + vy) * g.vn[0] + vx)]) key |= 1ull << bit;
+          }
+      auto it = seen.find(key);
+      if (it == seen.end()) {
+        it = seen.emplace(key, (int32_t)rep.size()).first;
+        rep.push_back(ci);
+      }
+      s.cut_mat[ci] = it->second;
+    }
+  }
+  s.n_cut_mat = (int64_t)rep.size();
+
+  // cut-cell matrices
+  s.Kcut.assign((size_t)s.n_cut_mat * nl * nl, 0.0);
+  s.mlcut.assign((size_t)s.n_cut_mat * nl, 0.0);
+  if (in.need_consistent_mass) s.Mcut.assign((size_t)s.n_cut_mat * nl * nl, 0.0);
+  parallel_for(s.n_cut_mat, [&](int64_t a, int64_t b) {
     std::vector<double> M(nl * nl), Ms(nl * nl), V(nl * nl), ev(nl);
-    for (int64_t ci = a; ci < b; ++ci) {
-      int64_t e = s.cut_cells[ci];
+    for (int64_t ci = a; ci < b; ++ci) {   // ci: matrix index
+      int64_t e = s.cut_cells[rep[ci]];
       double clo[3] = {0, 0, 0};
       int64_t rem = e;
       for (int k = 0; k < s.dim; ++k) {
@@ -779,7 +825,7 @@ Setup build_setup(const SetupInput& in) {
   s.ML.assign(s.n_lat_dof, 0.0);
   for (int64_t e = 0; e < s.n_elem; ++e) {
     if (s.cls[e] == kOutside) continue;
-    const double* ml = s.cls[e] == kCut ? &s.mlcut[(size_t)s.cut_index[e] * nl] : s.mref.data();
+    const double* ml = s.cls[e] == kCut ? &s.mlcut[(size_t)s.cut_mat[s.cut_index[e]] * nl] : s.mref.data();
     for (int l = 0; l < s.nn_loc; ++l) {
       int64_t node = lattice_node(s, e, l);
       for (int c = 0; c < s.ncomp; ++c) s.ML[node * s.ncomp + c] += ml[l * s.ncomp + c];
@@ -1018,8 +1064,8 @@ void imex_partition(const Setup& s, ImexData& d) {
     for (int l = 0; l < s.nn_loc; ++l)
       for (int c = 0; c < nc; ++c) loc_dof[l * nc + c] = d.c_of_dof[lattice_node(s, e, l) * nc + c];
     bool cut = s.cls[e] == kCut;
-    const double* K = cut ? &s.Kcut[(size_t)s.cut_index[e] * nl * nl] : s.Kref.data();
-    const double* M = cut ? &s.Mcut[(size_t)s.cut_index[e] * nl * nl] : nullptr;
+    const double* K = cut ? &s.Kcut[(size_t)s.cut_mat[s.cut_index[e]] * nl * nl] : s.Kref.data();
+    const double* M = cut ? &s.Mcut[(size_t)s.cut_mat[s.cut_index[e]] * nl * nl] : nullptr;
     for (int a = 0; a < nl; ++a) {
       if (loc_dof[a] < 0) continue;
       for (int b = 0; b < nl; ++b) {

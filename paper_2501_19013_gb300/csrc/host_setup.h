@@ -58,9 +58,13 @@ struct Setup {
   std::vector<double> Kref;          // n_loc^2
   std::vector<double> mref;          // n_loc, GLL lumped
   double lambda_ref = 0;
-  std::vector<double> Kcut;          // n_cut * n_loc^2, row-major, symmetric
-  std::vector<double> Mcut;          // n_cut * n_loc^2 consistent (alpha) mass (if kept)
-  std::vector<double> mlcut;         // n_cut * n_loc lumped (HRZ [+EVS] [x scale])
+  // cut-cell matrices, one set per distinct cut cell: cut cells of a voxel geometry whose
+  // voxel sub-images are equal have equal integrals and share one set
+  std::vector<int32_t> cut_mat;      // cut index -> matrix index
+  int64_t n_cut_mat = 0;
+  std::vector<double> Kcut;          // n_cut_mat * n_loc^2, row-major, symmetric
+  std::vector<double> Mcut;          // n_cut_mat * n_loc^2 consistent (alpha) mass (if kept)
+  std::vector<double> mlcut;         // n_cut_mat * n_loc lumped (HRZ [+EVS] [x scale])
   std::vector<double> ML;            // lattice dof -> assembled lumped mass (0 = dead)
   // 1D GLL data
   std::vector<double> gll_x, gll_w;

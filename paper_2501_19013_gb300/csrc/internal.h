@@ -17,10 +17,11 @@ struct DevProblem {
   const uint8_t* cls;       // per cell: 0 outside, 1 cut, 2 uncut
   const int32_t* cut_index; // per cell
   const int64_t* cut_cell;  // cut index -> cell
+  const int32_t* cut_mat;   // cut index -> matrix index of Kcut / Kcut32 (null: the same index)
   int n_cut;
   const double* Kref;       // n_loc^2 (symmetric)
-  const double* Kcut;       // n_cut * n_loc^2 (symmetric, row-major)
-  const float* Kcut32;      // per cut cell: n_loc^2 interleaved FP32 (hi, lo) pairs
+  const double* Kcut;       // per cut matrix n_loc^2 (symmetric, row-major)
+  const float* Kcut32;      // per cut matrix: n_loc^2 interleaved FP32 (hi, lo) pairs
   double* Ycut;             // n_cut * n_loc: K^e x_e of the cut cells for the current step
   const double* minv;       // dt^2 / M_L per lattice DOF (0 = dead); -(c + 1) marks IMEX c-DOF c
   const double* sinv;       // 1 / sqrt(M_L) per lattice DOF (0 = dead or IMEX c-DOF)

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) cut_apply_fp64_kernel(DevProblem pb, OpIn
       xs[warp][j] = load_in(x, g * NC + comp, scal);
     }
     __syncwarp();
-    const double* K = pb.Kcut + (size_t)ce * NL * NL;
+    const double* K = pb.Kcut + (size_t)(pb.cut_mat ? pb.cut_mat[ce] : ce) * NL * NL;
     for (int i0 = 0; i0 < NL; i0 += 32) {
       int i = i0 + lane;
       if (i < NL) {

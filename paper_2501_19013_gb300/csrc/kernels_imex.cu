@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, Ime
     xs[warp][j] = x[g * NC + comp];
   }
   __syncwarp();
-  const double* K = pb.cls[cell] == 1 ? pb.Kcut + (size_t)pb.cut_index[cell] * NL * NL : pb.Kref;
+  const int32_t ci = pb.cls[cell] == 1 ? pb.cut_index[cell] : 0;
+  const double* K = pb.cls[cell] == 1 ? pb.Kcut + (size_t)(pb.cut_mat ? pb.cut_mat[ci] : ci) * NL * NL : pb.Kref;
   for (int i = lane; i < NL; i += 32) {
     double acc = 0.0;
     for (int j = 0; j < NL; ++j) acc = fma(K[(size_t)j * NL + i], xs[warp][j], acc);

@@ -715,7 +715,9 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
       const int64_t cell = ((int64_t)ez * pb.n[1] + ey) * pb.n[0] + ex;
       // K^e as (hi, lo) FP32 pairs, column j contiguous over the rows i; the lane's rows
       // run as independent chains and the loads of several columns are in flight together
-      const float2* K2 = reinterpret_cast<const float2*>(pb.Kcut32) + (size_t)pb.cut_index[cell] * NL * NL;
+      const int32_t ci = pb.cut_index[cell];
+      const float2* K2 =
+          reinterpret_cast<const float2*>(pb.Kcut32) + (size_t)(pb.cut_mat ? pb.cut_mat[ci] : ci) * NL * NL;
       constexpr int R = (NL + 31) / 32;
       float sacc[R], cacc[R];
 #pragma unroll

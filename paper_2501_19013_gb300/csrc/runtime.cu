@@ -103,6 +103,7 @@ void Handle::build_device() {
   pb.n_lat_dof = s.n_lat_dof;
   pb.cls = upload(s.cls);
   pb.cut_index = upload(s.cut_index);
+  pb.cut_mat = upload(s.cut_mat);
   pb.cut_cell = upload(s.cut_cells);
   pb.n_cut = (int)s.n_cut;
   pb.Kref = upload(s.Kref);
@@ -210,9 +211,9 @@ void Handle::build_device() {
     tc_img_host = img;
     tc_frow_host = frow;
     // cut matrices as interleaved (hi, lo) FP32 pairs: one 8-byte load per entry
-    std::vector<float> k32(2 * (size_t)s.n_cut * s.n_loc * s.n_loc);
+    std::vector<float> k32(2 * (size_t)s.n_cut_mat * s.n_loc * s.n_loc);
     const size_t nl2 = (size_t)s.n_loc * s.n_loc;
-    for (int64_t c = 0; c < s.n_cut; ++c)
+    for (int64_t c = 0; c < s.n_cut_mat; ++c)
       for (size_t q = 0; q < nl2; ++q) {
         double v = s.Kcut[c * nl2 + q];
         float h = (float)v;
@@ -262,10 +263,10 @@ void Handle::build_device() {
 size_t Handle::planned_device_bytes() const {
   const Setup& s = setup;
   auto arr = [](int64_t count, size_t elem) { return (size_t)std::max<int64_t>(count, 1) * elem; };
-  const int64_t nl = s.n_loc, nlat = s.n_lat_dof, ncut = s.n_cut, nel = s.n_elem;
+  const int64_t nl = s.n_loc, nlat = s.n_lat_dof, ncut = s.n_cut, nel = s.n_elem, nmat = s.n_cut_mat;
   size_t b = 0;
-  b += arr(nel, 1) + arr(nel, 4) + arr(ncut, 8);          // cls, cut_index, cut_cells
-  b += arr(nl * nl, 8) + arr(ncut * nl * nl, 8);          // Kref, Kcut
+  b += arr(nel, 1) + arr(nel, 4) + arr(ncut, 8) + arr(ncut, 4);   // cls, cut_index, cut_cells, cut_mat
+  b += arr(nl * nl, 8) + arr(nmat * nl * nl, 8);          // Kref, Kcut
   b += arr(ncut, 8) * nl;                                 // Ycut
   b += 2 * arr(nlat, 8);                                  // minv, sinv
   if (imex) {
@@ -290,7 +291,7 @@ size_t Handle::planned_device_bytes() const {
     int64_t ntc = 1;
     for (int k = 0; k < s.dim; ++k) ntc *= (s.n[k] + tt[k] - 1) / tt[k];
     b += arr(ntc, 4);                                     // tile order
-    b += arr(2 * ncut * nl * nl, 4) + arr(2 * nlat, 4);   // Kcut32, minv32
+    b += arr(2 * nmat * nl * nl, 4) + arr(2 * nlat, 4);   // Kcut32, minv32
   }
   b += 64 + kPowerChunk * 8 + arr(nlat, 8);               // scalars, lam_hist, scratch
   return b;
@@ -639,6 +640,7 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
     out->n_levels = (int32_t)h->imex_host.chol.fwd_level_ptr.size() - 1;
   }
   out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes;
+  out->n_cut_matrices = s.n_cut_mat;
   return IBFEM_OK;
 }
 
@@ -891,7 +893,7 @@ int ibfem_set_initial(ibfem_t* h, const double* u0, const double* v0) {
           dofs[l * nc + c] = lattice_node(s, e, l) * nc + c;
           xe[l * nc + c] = lu[dofs[l * nc + c]];
         }
-      const double* K = s.cls[e] == kCut ? &s.Kcut[(size_t)s.cut_index[e] * nl * nl] : s.Kref.data();
+      const double* K = s.cls[e] == kCut ? &s.Kcut[(size_t)s.cut_mat[s.cut_index[e]] * nl * nl] : s.Kref.data();
       for (int a = 0; a < nl; ++a) {
         int64_t ci = I.c_of_dof[dofs[a]];
         if (ci < 0) continue;
@@ -1143,7 +1145,7 @@ int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml) {
   if (cell < 0 || cell >= s.n_elem || s.cls[cell] == kOutside) return fail(IBFEM_ERR_ARG, "cell is outside or out of range");
   const int nl = s.n_loc;
   if (s.cls[cell] == kCut) {
-    int ci = s.cut_index[cell];
+    int ci = s.cut_mat[s.cut_index[cell]];
     if (K) std::copy(&s.Kcut[(size_t)ci * nl * nl], &s.Kcut[(size_t)(ci + 1) * nl * nl], K);
     if (ml) std::copy(&s.mlcut[(size_t)ci * nl], &s.mlcut[(size_t)(ci + 1) * nl], ml);
   } else {

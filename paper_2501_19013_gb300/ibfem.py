@@ -62,7 +62,8 @@ class Info(C.Structure):
                 ("n_c", C.c_int64), ("nnz_L", C.c_int64), ("n_levels", C.c_int32),
                 ("n_loc", C.c_int32), ("ncomp", C.c_int32), ("precision", C.c_int32),
                 ("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double),
-                ("lambda_ref", C.c_double), ("device_bytes", C.c_size_t)]
+                ("lambda_ref", C.c_double), ("device_bytes", C.c_size_t),
+                ("n_cut_matrices", C.c_int64)]
 
 
 _lib = None

@@ -70,3 +70,21 @@ def test_imex_partition_size():
     s = ib.from_workload(w, host_only=True)
     assert s.info().n_c == len(d.c_dofs())
     s.close()
+
+
+def test_voxel_blocks_share_cut_matrices():
+    # cut cells with equal voxel blocks (2 voxels per cell and axis) share one matrix set;
+    # every cut cell's shared set must equal the oracle's own integration of that cell
+    w = W.porous_voxel(n=8, vn=16, p=2, steps=10)
+    d = OD.from_workload(w)
+    s = ib.from_workload(w, host_only=True)
+    inf = s.info()
+    assert inf.n_cut_matrices < inf.n_cut
+    for e in d.cut:
+        K, m = s.element(e)
+        np.testing.assert_allclose(K, d.K_cut[e], rtol=1e-11, atol=1e-11 * np.abs(d.K_cut[e]).max())
+        np.testing.assert_allclose(m, d.ml_cut[e], rtol=1e-9, atol=1e-9 * m.max())
+    s.close()
+    h = ib.from_workload(W.plate_one_hole(), host_only=True)
+    assert h.info().n_cut_matrices == h.info().n_cut   # curved boundaries: no sharing
+    h.close()
