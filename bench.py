@@ -110,6 +110,8 @@ def workload_for_bench():
         return W.porous_voxel(n=GRID if GRID != 256 else 64)
     if WORKLOAD == "plate_one_hole":
         return W.plate_one_hole()
+    if WORKLOAD == "rotated_cube":
+        return W.rotated_cube(ne=GRID if GRID != 256 else 13)
     return W.plate_holes_elastic(n=GRID)
 
 
@@ -406,7 +408,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=32, help="maximum concurrent members of the batch")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory budget of the serving run")
     ap.add_argument("--workload", default="plate_holes_elastic",
-                    choices=["plate_holes_elastic", "plate_holes_imex", "porous_voxel", "plate_one_hole"])
+                    choices=["plate_holes_elastic", "plate_holes_imex", "porous_voxel", "plate_one_hole",
+                             "rotated_cube"])
     args = ap.parse_args()
     global GRID, WORKLOAD
     GRID = args.grid

@@ -68,7 +68,8 @@ enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores          
        IBFEM_BF16_TC = 3        /* tcgen05 kind::f16, one BF16 pass, FP32 accumulation      */ };
 enum { IBFEM_SRC_NONE = 0,
        IBFEM_SRC_POINT = 1,          /* params: x, y[, z] [, dir_x, dir_y] (elastic)   */
-       IBFEM_SRC_EDGE_TRACTION = 2   /* params: y0, y1, t_x[, t_y]; edge x = lo_x (2D) */ };
+       IBFEM_SRC_EDGE_TRACTION = 2,  /* params: y0, y1, t_x[, t_y]; edge x = lo_x (2D) */
+       IBFEM_SRC_GAUSS = 3           /* params: x_l[dim], sigma (volumetric Gaussian)  */ };
 
 /* ---- structures ------------------------------------------------------------------ */
 typedef struct ibfem_s ibfem_t;
@@ -156,7 +157,11 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out);
 /* Load F^k = F_s * f_t(t_k) with the Ricker wavelet of Eq. source_time (centre
  * frequency f_e).  kind/params as in IBFEM_SRC_*.  A point source contributes
  * alpha^FCM(x_s) rho N_i(x_s) (times the direction for elasticity); an edge traction
- * contributes the boundary integral of alpha^FCM N_i t.  Errors: ARG, GEOMETRY.        */
+ * contributes the boundary integral of alpha^FCM N_i t; the Gaussian load of the
+ * benchmark (Sec. 3.1) contributes int alpha^FCM rho f_s N_i over the kept cells with
+ * f_s = exp(-|x - x_l|^2 / (2 sigma^2)) (Eq. weak_form_extended, load term), integrated on
+ * cells within 8 sigma of x_l split into ceil(h / sigma)^dim subcells with (p + 4)^dim
+ * Gauss-Legendre points each.  Errors: ARG, GEOMETRY.                                   */
 int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, double f_e);
 
 /* Observer points (Sec. 3.2): npts x dim coordinates.  Each step records

@@ -14,7 +14,9 @@ node's ncomp DOFs are consecutive (node-major).
 Loads (Sec. 3.1, Eq. source_time): a Ricker wavelet f_t(t) = (1 - 2 q^2) exp(-q^2) with
 q = pi f_e (t - t_s), t_s = 2 sqrt(6) / (pi f_e), times a spatial vector: a point source
 F_i = alpha^FCM(x_s) rho N_i(x_s) (times a direction for elasticity) or an edge traction
-F_i = int_Gamma alpha^FCM N_i t ds on the boundary x = lo_x, y in [y0, y1].
+F_i = int_Gamma alpha^FCM N_i t ds on the boundary x = lo_x, y in [y0, y1], or the
+volumetric Gaussian load of the benchmark (Sec. 3.1), F_i = int alpha^FCM rho f_s N_i dx with
+f_s = exp(-|x - x_l|^2 / (2 sigma^2)).
 
 Observers (Sec. 3.2): Psi(x) = sum_j N_j(x) Psi_j in the lowest-numbered kept cell that
 contains x.
@@ -342,6 +344,46 @@ class Discretization:
                 F[nodes * self.ncomp + c] += integ * t[c if len(t) > c else 0]
         return F
 
+    def gauss_load(self, x_l, sigma):
+        """F_i = int over the kept cells of alpha^FCM rho f_s N_i, f_s the Gaussian of Sec. 3.1
+        (weak form Eq. weak_form_extended, load term).
+
+        Quadrature (the paper does not give one; reading shared with the library): every
+        kept cell whose box lies within 8 sigma of x_l is split into m^d equal subcells,
+        m = max(1, ceil(max_k h_k / sigma)), each integrated with (p + 4)^d Gauss-Legendre
+        points, alpha^FCM evaluated at the points.  Beyond 8 sigma f_s < 1.3e-14."""
+        x_l = np.asarray(x_l, dtype=np.float64)
+        reach = 8.0 * sigma
+        m = max(1, int(math.ceil(float(np.max(self.h)) / sigma)))
+        xg, wg = gauss_legendre(self.p + 4)
+        F = np.zeros(self.n_dof)
+        for e in range(int(np.prod(self.n))):
+            if self.cls[e] == OUTSIDE:
+                continue
+            lo, hi = self.elem_box(e)
+            gap = np.maximum(np.maximum(lo - x_l, x_l - hi), 0.0)
+            if np.sqrt(np.sum(gap * gap)) > reach:
+                continue
+            # composite 1D rules per axis (m subintervals), then the tensor grid
+            pts, wts = [], []
+            for k in range(self.dim):
+                a = lo[k] + (hi[k] - lo[k]) * np.arange(m) / m
+                b = lo[k] + (hi[k] - lo[k]) * np.arange(1, m + 1) / m
+                pts.append((a[:, None] + (xg[None, :] + 1.0) * 0.5 * (b - a)[:, None]).ravel())
+                wts.append((np.repeat(0.5 * (b - a), len(xg)) * np.tile(wg, m)))
+            grids = np.meshgrid(*pts, indexing="ij")
+            X = np.stack([g.ravel() for g in grids], axis=1)
+            Wg = np.meshgrid(*wts, indexing="ij")
+            Wq = np.prod(np.stack([g.ravel() for g in Wg], axis=1), axis=1)
+            A = np.ones(len(X)) if self.geom is None else np.where(self.geom.in_physical(X), 1.0, self.alpha)
+            f = np.exp(-0.5 * np.sum((X - x_l[None, :]) ** 2, axis=1) / (sigma * sigma))
+            N, _ = el.shape_functions(self.p, lo, hi, X)
+            integ = (Wq * A * f * self.rho) @ N
+            nodes = self.node_of_lattice[self.elem_lat[e]]
+            for c in range(self.ncomp):
+                F[nodes * self.ncomp + c] += integ
+        return F
+
     def observer_matrix(self, pts):
         """Sparse (n_obs * ncomp, n_dof) interpolation: row o*ncomp + c samples comp c."""
         rows, cols, vals = [], [], []
@@ -368,7 +410,8 @@ class Discretization:
 
 def from_workload(w, **over):
     """Build a Discretization for a ``workloads.Workload``."""
-    geom = make_geometry(w.dim, holes=w.holes, voxels=w.voxels, lo=w.lo, hi=w.hi)
+    geom = make_geometry(w.dim, holes=w.holes, voxels=w.voxels, lo=w.lo, hi=w.hi,
+                         rotated_box=getattr(w, "rotated_box", None))
     kw = dict(dim=w.dim, n=w.n, p=w.p, physics=w.physics, geometry=geom, alpha=w.alpha,
               quad_depth=w.quad_depth, stab=w.stab, eps=w.eps, f_lambda=w.f_lambda,
               rho=w.rho, c=w.c, E=w.E, nu=w.nu, lo=w.lo, hi=w.hi)
@@ -382,4 +425,6 @@ def source_vector(disc, src):
         return disc.point_load(np.asarray(src["x"], float), src.get("dir"))
     if kind == "edge_traction":
         return disc.edge_traction_load(src["y0"], src["y1"], src.get("t", [1.0, 0.0]))
+    if kind == "gauss":
+        return disc.gauss_load(np.asarray(src["x"], float), float(src["sigma"]))
     raise ValueError(kind)

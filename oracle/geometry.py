@@ -164,7 +164,10 @@ class RotatedBox:
         return np.all(np.abs(loc) <= self.half, axis=1)
 
 
-def make_geometry(dim, holes=None, voxels=None, lo=None, hi=None):
+def make_geometry(dim, holes=None, voxels=None, lo=None, hi=None, rotated_box=None):
+    if rotated_box is not None:
+        rb = np.asarray(rotated_box, dtype=np.float64)
+        return RotatedBox(rb[0], rb[1:4], rb[4:13].reshape(3, 3))
     if voxels is not None:
         return Voxels(voxels, lo, hi)
     if holes is not None and len(holes) > 0:

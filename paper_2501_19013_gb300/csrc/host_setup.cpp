@@ -583,6 +583,76 @@ double indicator(const SetupInput& in, const double* x) {
   return g.physical_point(x) ? 1.0 : in.alpha;
 }
 
+void gauss_load(const Setup& s, const SetupInput& in, const double* xl, double sigma,
+                std::vector<int64_t>& dofs, std::vector<double>& vals) {
+  // kept cells within 8 sigma of x_l (f_s < 1.3e-14 beyond); each split into m^d subcells,
+  // m = max(1, ceil(max_k h_k / sigma)), with (p + 4)-point Gauss-Legendre rules per axis
+  Geo geo(in);
+  const double reach = 8.0 * sigma;
+  double hmax = 0.0;
+  for (int k = 0; k < s.dim; ++k) hmax = std::max(hmax, s.h[k]);
+  const int m = std::max(1, (int)std::ceil(hmax / sigma));
+  std::vector<double> xg, wg;
+  gauss_rule(s.p + 4, xg, wg);
+  const int nq = (int)xg.size(), n1 = m * nq;   // points per axis and cell
+  std::vector<double> px(3 * n1), pw(3 * n1), L(3 * (size_t)n1 * s.nn1);
+  std::vector<double> acc(s.nn_loc);
+  for (int64_t e = 0; e < s.n_elem; ++e) {
+    if (s.cls[e] == kOutside) continue;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, gap2 = 0.0;
+    int64_t rem = e;
+    for (int k = 0; k < s.dim; ++k) {
+      lo[k] = s.lo[k] + (rem % s.n[k]) * s.h[k];
+      hi[k] = lo[k] + s.h[k];
+      rem /= s.n[k];
+      const double g = std::max(std::max(lo[k] - xl[k], xl[k] - hi[k]), 0.0);
+      gap2 += g * g;
+    }
+    if (std::sqrt(gap2) > reach) continue;
+    // composite points and weights per axis, and the 1D basis values at them
+    for (int k = 0; k < s.dim; ++k)
+      for (int a = 0; a < m; ++a) {
+        const double sa = lo[k] + (hi[k] - lo[k]) * a / m, sb = lo[k] + (hi[k] - lo[k]) * (a + 1) / m;
+        for (int q = 0; q < nq; ++q) {
+          const int i = a * nq + q;
+          px[k * n1 + i] = sa + (xg[q] + 1.0) * 0.5 * (sb - sa);
+          pw[k * n1 + i] = wg[q] * 0.5 * (sb - sa);
+          lagrange1d(s.gll_x, 2.0 * (px[k * n1 + i] - lo[k]) / s.h[k] - 1.0, &L[((size_t)k * n1 + i) * s.nn1], nullptr);
+        }
+      }
+    std::fill(acc.begin(), acc.end(), 0.0);
+    const int nz = s.dim == 3 ? n1 : 1;
+    for (int iz = 0; iz < nz; ++iz)
+      for (int iy = 0; iy < n1; ++iy)
+        for (int ix = 0; ix < n1; ++ix) {
+          const int idx[3] = {ix, iy, iz};
+          double x[3] = {0, 0, 0}, w = in.rho, r2 = 0.0;
+          for (int k = 0; k < s.dim; ++k) {
+            x[k] = px[k * n1 + idx[k]];
+            w *= pw[k * n1 + idx[k]];
+            r2 += (x[k] - xl[k]) * (x[k] - xl[k]);
+          }
+          w *= std::exp(-0.5 * r2 / (sigma * sigma)) * (geo.physical_point(x) ? 1.0 : in.alpha);
+          for (int j = 0; j < s.nn_loc; ++j) {
+            int jj = j;
+            double v = w;
+            for (int k = 0; k < s.dim; ++k) {
+              v *= L[((size_t)k * n1 + idx[k]) * s.nn1 + jj % s.nn1];
+              jj /= s.nn1;
+            }
+            acc[j] += v;
+          }
+        }
+    for (int l = 0; l < s.nn_loc; ++l) {
+      if (acc[l] == 0.0) continue;
+      for (int c = 0; c < s.ncomp; ++c) {
+        dofs.push_back(lattice_node(s, e, l) * s.ncomp + c);
+        vals.push_back(acc[l]);
+      }
+    }
+  }
+}
+
 void edge_traction(const Setup& s, const SetupInput& in, double y0, double y1,
                    const double* t, std::vector<int64_t>& dofs, std::vector<double>& vals) {
   Geo geo(in);

@@ -85,6 +85,11 @@ int64_t lattice_node(const Setup& s, int64_t cell, int loc);
 // alpha^FCM at a point (1 inside the physical domain).
 double indicator(const SetupInput& in, const double* x);
 
+// Volumetric Gaussian load of the benchmark (Sec. 3.1): int alpha^FCM rho f_s N_i over the
+// kept cells, f_s = exp(-|x - xl|^2 / (2 sigma^2)); (lattice dof, value) pairs.
+void gauss_load(const Setup& s, const SetupInput& in, const double* xl, double sigma,
+                std::vector<int64_t>& dofs, std::vector<double>& vals);
+
 // Edge-traction load on x = lo_x, y in [y0, y1]: returns (lattice dof, value) pairs.
 void edge_traction(const Setup& s, const SetupInput& in, double y0, double y1,
                    const double* t, std::vector<int64_t>& dofs, std::vector<double>& vals);

@@ -683,6 +683,12 @@ int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, do
         dofs.push_back(lattice_node(s, cell, l) * s.ncomp + c);
         vals.push_back(v);
       }
+  } else if (kind == IBFEM_SRC_GAUSS) {
+    if (!params || nparams < s.dim + 1 || !(params[s.dim] > 0))
+      throw std::invalid_argument("Gaussian load needs (x_l[dim], sigma > 0)");
+    double xl[3] = {0, 0, 0};
+    for (int k = 0; k < s.dim; ++k) xl[k] = params[k];
+    gauss_load(s, h->input, xl, params[s.dim], dofs, vals);
   } else if (kind == IBFEM_SRC_EDGE_TRACTION) {
     if (s.dim != 2 || !params || nparams < 3) throw std::invalid_argument("edge traction needs (y0, y1, t_x[, t_y]) in 2D");
     double t[2] = {params[2], nparams >= 4 ? params[3] : 0.0};

@@ -21,7 +21,7 @@ STAB_NONE, STAB_EVS, STAB_MASS_SCALING = 0, 1, 2
 SCALAR, ELASTIC_PLANE_STRAIN = 0, 1
 CDM, IMEX = 0, 1
 FP64, EXACT_TC, BF16X3_TC, BF16_TC = 0, 1, 2, 3
-SRC_NONE, SRC_POINT, SRC_EDGE_TRACTION = 0, 1, 2
+SRC_NONE, SRC_POINT, SRC_EDGE_TRACTION, SRC_GAUSS = 0, 1, 2, 3
 
 PRECISIONS = {"fp64": FP64, "exact": EXACT_TC, "bf16x3": BF16X3_TC, "bf16": BF16_TC}
 
@@ -232,7 +232,7 @@ class Solver:
         return i
 
     def set_source(self, kind, params, f_e):
-        k = {"none": SRC_NONE, "point": SRC_POINT, "edge_traction": SRC_EDGE_TRACTION}[kind]
+        k = {"none": SRC_NONE, "point": SRC_POINT, "edge_traction": SRC_EDGE_TRACTION, "gauss": SRC_GAUSS}[kind]
         pr = _f64(params) if params is not None else np.zeros(1)
         _check(lib().ibfem_set_source(self.h, k, _dp(pr), len(pr) if params is not None else 0, f_e))
 
@@ -376,6 +376,7 @@ def from_workload(w, precision="fp64", host_only=False, scheme=None, **kw):
     """Create a Solver for a ``workloads.Workload`` (geometry and material only)."""
     return Solver(w.dim, w.n, w.p, lo=w.lo, hi=w.hi, physics=w.physics, rho=w.rho, c=w.c,
                   E=w.E, nu=w.nu, alpha=w.alpha, holes=w.holes, voxels=w.voxels,
+                  rotated_box=getattr(w, "rotated_box", None),
                   quad_depth=w.quad_depth, stab=w.stab, eps=w.eps, f_lambda=w.f_lambda,
                   scheme=scheme or w.scheme, precision=precision, host_only=host_only, **kw)
 
@@ -384,4 +385,6 @@ def source_params(w):
     s = w.source
     if s.get("kind", "point") == "point":
         return "point", list(s["x"]) + list(s.get("dir", []))
+    if s["kind"] == "gauss":
+        return "gauss", list(s["x"]) + [s["sigma"]]
     return "edge_traction", [s["y0"], s["y1"]] + list(s.get("t", [1.0, 0.0]))

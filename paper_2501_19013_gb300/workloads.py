@@ -135,6 +135,7 @@ class Workload:
     quad_depth: int = 3
     holes: Optional[np.ndarray] = None   # (k, d+1) rows (centre..., r)
     voxels: Optional[np.ndarray] = None  # uint8 [z, y, x], 1 = void
+    rotated_box: Optional[np.ndarray] = None  # (edge, centre[3], T[9] row-major): x = c + T x' 
     stab: str = "none"                # "none" | "evs" | "mass_scaling"
     eps: float = 0.0
     f_lambda: float = 1e-2
@@ -283,9 +284,47 @@ def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
     return out
 
 
+def rotation_zyx(phi: float, theta: float, psi: float) -> np.ndarray:
+    """Rotation of the cube's local frame, Cardan angles (radians) taken as intrinsic
+    rotations about z, then y, then x: T = R_z(phi) R_y(theta) R_x(psi)."""
+    cz, sz = math.cos(phi), math.sin(phi)
+    cy, sy = math.cos(theta), math.sin(theta)
+    cx, sx = math.cos(psi), math.sin(psi)
+    Rz = np.array([[cz, -sz, 0.0], [sz, cz, 0.0], [0.0, 0.0, 1.0]])
+    Ry = np.array([[cy, 0.0, sy], [0.0, 1.0, 0.0], [-sy, 0.0, cy]])
+    Rx = np.array([[1.0, 0.0, 0.0], [0.0, cx, -sx], [0.0, sx, cx]])
+    return Rz @ Ry @ Rx
+
+
+def rotated_cube(ne: int = 13, p: int = 3, alpha: float = 1e-12, stab: str = "evs",
+                 eps: float = 1e-4, quad_depth: int = 3, steps: int = 2000) -> Workload:
+    """The paper's benchmark (Sec. 3.1): a cube of edge 0.3 rotated by the Cardan angles
+    (10, 10, 10) degrees about the centre of the extended cube [0, 0.5]^3, scalar wave
+    (rho = c = 1), a Gaussian volumetric load (sigma = 0.01) centred on one face of the
+    cube times a Ricker wavelet (f_e = 10), and the 11 observers of the paper's table of
+    observer locations (source, centre, face, 4 edge centres, 4 corners)."""
+    lp, le = 0.3, 0.5
+    T = rotation_zyx(*(math.radians(10.0),) * 3)
+    c = np.full(3, le / 2.0)
+    xs = c + T @ np.array([-lp / 2.0, 0.0, 0.0])
+    # observer table in the cube's corner-based local frame [0, l]^3, then centred
+    loc = [(0.0, 0.5, 0.5), (0.5, 0.5, 0.5), (1.0, 0.5, 0.5)]
+    loc += [(0.5, 0.5 + a, 0.5 + b) for a in (-0.5, 0.5) for b in (-0.5, 0.5)]
+    loc += [(1.0, 0.5 + a, 0.5 + b) for a in (-0.5, 0.5) for b in (-0.5, 0.5)]
+    obs = np.array([c + T @ ((np.array(q) - 0.5) * lp) for q in loc])
+    # corners and edges lie on the immersed boundary: pull them 1e-9 into the cube
+    obs = np.array([c + (x - c) * (1.0 - 1e-9) for x in obs])
+    return Workload(name=f"rotated_cube_{ne}^3_p{p}", dim=3, n=(ne, ne, ne), p=p,
+                    physics="scalar", alpha=alpha, quad_depth=quad_depth,
+                    rotated_box=np.concatenate([[lp], c, T.ravel()]), stab=stab, eps=eps,
+                    f_lambda=1e-2, source={"kind": "gauss", "x": list(xs), "sigma": 0.01},
+                    f0=10.0, steps=steps, observers=obs, hi=(le, le, le))
+
+
 WORKLOADS = {
     "plate_one_hole": plate_one_hole,
     "plate_holes_elastic": plate_holes_elastic,
     "plate_holes_imex": plate_holes_imex,
     "porous_voxel": porous_voxel,
+    "rotated_cube": rotated_cube,
 }

@@ -55,4 +55,5 @@ SMALL_CASES = {
     "scalar_mass_scaling": lambda: W.plate_holes_imex(n=30, p=3, count=3, scheme="cdm", steps=200),
     "voxel_3d_evs": lambda: W.porous_voxel(n=6, vn=12, p=3, steps=100),
     "voxel_3d_p2_ragged": lambda: W.porous_voxel(n=7, vn=14, p=2, seed=2, steps=100),
+    "rotated_cube_gauss": lambda: W.rotated_cube(ne=6, p=2, quad_depth=2, steps=120),
 }
