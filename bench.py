@@ -181,9 +181,12 @@ def run_serving(args):
 
 def parse_variant(v, w):
     """'fp64' | 'exact' | 'bf16x3' | 'bf16' -> CDM with the workload's stabilisation;
-    'imex' -> Newmark IMEX (FP64); 'ms:<precision>' -> CDM with mass scaling."""
+    'imex' -> Newmark IMEX (FP64); 'cons' -> CDM with the consistent cut mass (FP64);
+    'ms:<precision>' -> CDM with mass scaling."""
     if v == "imex":
         return w.with_(scheme="imex", stab="none"), "fp64"
+    if v == "cons":
+        return w.with_(scheme="cdm_consistent"), "fp64"
     if v.startswith("ms:"):
         return w.with_(scheme="cdm", stab="mass_scaling"), v[3:]
     return w.with_(scheme="cdm" if w.scheme != "imex" else "cdm",

@@ -57,7 +57,13 @@ enum { IBFEM_GEOM_NONE = 0,     /* no immersed boundary: every cell is uncut    
        IBFEM_GEOM_ROTATED_BOX = 3 /* physical domain = rotated cube (Sec. 3.1)          */ };
 enum { IBFEM_STAB_NONE = 0, IBFEM_STAB_EVS = 1, IBFEM_STAB_MASS_SCALING = 2 };
 enum { IBFEM_SCALAR = 0, IBFEM_ELASTIC_PLANE_STRAIN = 1 };
-enum { IBFEM_CDM = 0, IBFEM_IMEX = 1 };
+/* Time integration: IBFEM_CDM, Eq. cdm with the lumped mass; IBFEM_IMEX, Algorithm 2
+ * (Newmark beta = 1/4, gamma = 1/2 on the DOFs of cut cells, CDM on the rest);
+ * IBFEM_CDM_CONSISTENT, the central-difference method with the consistent mass of the cut
+ * cells (the paper's "SCM con." CDM): Algorithm 2 with beta = 0, i.e. the DOFs of cut cells
+ * are advanced explicitly through a solve with their consistent (EVS-stabilised when
+ * eps > 0) mass block M^cc. */
+enum { IBFEM_CDM = 0, IBFEM_IMEX = 1, IBFEM_CDM_CONSISTENT = 2 };
 /* Precision of the element contractions.  The integrator state (u^k, u^{k-1}), the
  * central-difference update, the IMEX solves and the power iteration are FP64 always. */
 enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores                      */
@@ -102,7 +108,7 @@ typedef struct {
     int physics;              /* IBFEM_SCALAR or IBFEM_ELASTIC_PLANE_STRAIN (2D only)  */
     double rho, c;            /* density, wave speed (scalar)                          */
     double E, nu;             /* Young's modulus, Poisson ratio (elastic)              */
-    int scheme;               /* IBFEM_CDM or IBFEM_IMEX                               */
+    int scheme;               /* IBFEM_CDM, IBFEM_IMEX or IBFEM_CDM_CONSISTENT         */
     int precision;            /* IBFEM_FP64 / _EXACT_TC / _BF16X3_TC / _BF16_TC         */
     void* stream;             /* cudaStream_t to run on, NULL = the legacy stream      */
     void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator         */

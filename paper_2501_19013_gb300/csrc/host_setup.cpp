@@ -855,7 +855,6 @@ Setup build_setup(const SetupInput& in) {
       }
       double* K = &s.Kcut[(size_t)ci * nl * nl];
       integ.cut_cell(geo, e, clo, K, M.data());
-      if (in.need_consistent_mass) std::copy(M.begin(), M.end(), &s.Mcut[(size_t)ci * nl * nl]);
       // eigenvalue stabilisation M^e = M^o + eps M^s (Eq. epsilon_stabilization)
       if (in.stab == 1) {
         std::copy(M.begin(), M.end(), Ms.begin());
@@ -877,6 +876,9 @@ Setup build_setup(const SetupInput& in) {
           for (int i = 0; i < nl * nl; ++i) M[i] += sc * Ms[i];
         }
       }
+      // the consistent cut mass of the IMEX / consistent-mass schemes: M^o, plus eps M^s
+      // with eigenvalue stabilisation
+      if (in.need_consistent_mass) std::copy(M.begin(), M.end(), &s.Mcut[(size_t)ci * nl * nl]);
       // HRZ lumping: diagonal scaled to the element's total mass
       double total = 0, tr = 0;
       for (int i = 0; i < nl * nl; ++i) total += M[i];

@@ -122,6 +122,12 @@ cudaError_t launch_cut_apply_fp64(const DevProblem& pb, OpInput x, bool sample, 
 // Launchers (kernels_imex.cu)
 cudaError_t launch_imex_cell_apply(const DevProblem& pb, const ImexDev& im, const double* x, cudaStream_t st);
 cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* out, cudaStream_t st);
+cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* scal, double* out, bool backward,
+                            cudaStream_t st);
+cudaError_t launch_scale_vec(int64_t n, const double* s, const double* in, const double* scal, double* out,
+                             cudaStream_t st);
+cudaError_t launch_dot2(int64_t n, const double* a, const double* scal, const double* b, double* partials,
+                        int nblocks, cudaStream_t st);
 cudaError_t launch_op_fp64(const DevProblem& pb, OpInput x, double* out, int mode,
                            double* partials, cudaStream_t st);
 cudaError_t launch_reduce_power(const double* partials, int nblocks, double* lam_hist,

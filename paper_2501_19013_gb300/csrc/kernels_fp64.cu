@@ -16,6 +16,8 @@
 // M_L^{-1/2} K M_L^{-1/2} w with deterministic per-CTA partial sums (Sec. 2.3).
 #include <cstdio>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace ibfem {
@@ -328,6 +330,53 @@ __global__ void reduce_power_kernel(const double* partials, int nblocks, double*
     lam_hist[iter] = sa[0];
     *inv_norm = sb[0] > 0.0 ? 1.0 / sqrt(sb[0]) : 0.0;
   }
+}
+
+// out = s .* in * (scal ? *scal : 1) over n entries
+__global__ void scale_vec_kernel(int64_t n, const double* __restrict__ sv, const double* __restrict__ in,
+                                 const double* __restrict__ scal, double* __restrict__ out) {
+  const double sc = scal ? *scal : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = sv[i] * in[i] * sc;
+}
+
+// per-block partial sums (fixed order) of (a * scal) . b and b . b
+__global__ void dot2_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ scal,
+                            const double* __restrict__ b, double* __restrict__ partials) {
+  __shared__ double sa[256], sb[256];
+  const double sc = scal ? *scal : 1.0;
+  double x = 0.0, y = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x = fma(a[i] * sc, b[i], x);
+    y = fma(b[i], b[i], y);
+  }
+  sa[threadIdx.x] = x;
+  sb[threadIdx.x] = y;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sa[threadIdx.x] += sa[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sa[0];
+    partials[2 * blockIdx.x + 1] = sb[0];
+  }
+}
+
+cudaError_t launch_scale_vec(int64_t n, const double* s, const double* in, const double* scal, double* out,
+                             cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  scale_vec_kernel<<<blocks, 256, 0, st>>>(n, s, in, scal, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot2(int64_t n, const double* a, const double* scal, const double* b, double* partials,
+                        int nblocks, cudaStream_t st) {
+  dot2_kernel<<<nblocks, 256, 0, st>>>(n, a, scal, b, partials);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ dispatch

@@ -115,6 +115,55 @@ __global__ void __launch_bounds__(1024) imex_solve_kernel(DevProblem pb, ImexDev
   }
 }
 
+// One triangular solve with the Cholesky factor L of S (permuted order), for the power
+// iteration of the consistent-mass CDM (S = M^cc there): one CTA per component; the right-
+// hand side is b[r] = in[c_dof[perm[r]]] * scal, the solution of L w = b (forward) or of
+// L^T w = b (backward) is written to out[c_dof[perm[r]]].
+__global__ void __launch_bounds__(1024) imex_tri_kernel(ImexDev im, const double* __restrict__ in,
+                                                        const double* __restrict__ scal,
+                                                        double* __restrict__ out, int backward) {
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int r0 = im.comp_ptr[b], r1 = im.comp_ptr[b + 1];
+  const double sc = scal ? *scal : 1.0;
+  double* w = im.work;
+  for (int r = r0 + tid; r < r1; r += blockDim.x) w[r] = in[im.c_dof[im.perm[r]]] * sc;
+  __syncthreads();
+  if (!backward) {
+    for (int lv = im.comp_flvl[b]; lv < im.comp_flvl[b + 1]; ++lv) {
+      for (int q = im.f_lvl[lv] + warp; q < im.f_lvl[lv + 1]; q += nwarps) {
+        const int r = im.f_rows[q];
+        const int64_t p0 = im.Lp[r], p1 = im.Lp[r + 1] - 1;  // diagonal stored last
+        double acc = 0.0;
+        for (int64_t p = p0 + lane; p < p1; p += 32) acc = fma(im.Lx[p], w[im.Li[p]], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) w[r] = (w[r] - acc) * im.dinv[r];
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int lv = im.comp_blvl[b]; lv < im.comp_blvl[b + 1]; ++lv) {
+      for (int q = im.b_lvl[lv] + warp; q < im.b_lvl[lv + 1]; q += nwarps) {
+        const int r = im.b_rows[q];
+        const int64_t p0 = im.Up[r] + 1, p1 = im.Up[r + 1];  // diagonal stored first
+        double acc = 0.0;
+        for (int64_t p = p0 + lane; p < p1; p += 32) acc = fma(im.Ux[p], w[im.Ui[p]], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) w[r] = (w[r] - acc) * im.dinv[r];
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = r0 + tid; r < r1; r += blockDim.x) out[im.c_dof[im.perm[r]]] = w[r];
+}
+
+cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* scal, double* out, bool backward,
+                            cudaStream_t st) {
+  if (im.n_comp == 0) return cudaSuccess;
+  imex_tri_kernel<<<im.n_comp, 1024, 0, st>>>(im, in, scal, out, backward ? 1 : 0);
+  return cudaGetLastError();
+}
+
 #define IBFEM_IMEX_SHAPES(X) \
   X(2, 1, 1) X(2, 2, 1) X(2, 3, 1) X(2, 4, 1) X(2, 5, 1) X(2, 6, 1) \
   X(2, 1, 2) X(2, 2, 2) X(2, 3, 2) X(2, 4, 2) X(3, 1, 1) X(3, 2, 1) X(3, 3, 1)

@@ -297,6 +297,14 @@ size_t Handle::planned_device_bytes() const {
   return b;
 }
 
+// consistent-mass CDM: S = M^cc does not depend on dt, so it is factored once
+void Handle::prepare_consistent() {
+  std::string err;
+  if (!imex_factor(setup, 0.0, imex_host, err)) throw std::runtime_error("consistent mass factorisation: " + err);
+  imex_upload_factor();
+  imex_dev.beta_dt2 = 0.0;
+}
+
 void Handle::imex_upload_factor() {
   const ImexData& I = imex_host;
   const SparseChol& L = I.chol;
@@ -491,6 +499,7 @@ void attach_device(ibfem_t* h) {
     h->own_stream = true;
   }
   h->build_device();
+  if (h->consistent && h->imex) h->prepare_consistent();
 }
 }  // namespace
 
@@ -529,10 +538,11 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   if (!(alpha >= 0.0)) throw std::invalid_argument("alpha must be >= 0");
   if (o.physics != IBFEM_SCALAR && o.physics != IBFEM_ELASTIC_PLANE_STRAIN)
     throw std::invalid_argument("unknown physics");
-  if (o.scheme != IBFEM_CDM && o.scheme != IBFEM_IMEX) throw std::invalid_argument("unknown scheme");
-  if (o.scheme == IBFEM_IMEX && o.precision != IBFEM_FP64)
-    throw std::invalid_argument("IMEX runs in FP64 (precision must be IBFEM_FP64)");
-  in.need_consistent_mass = o.scheme == IBFEM_IMEX;
+  if (o.scheme != IBFEM_CDM && o.scheme != IBFEM_IMEX && o.scheme != IBFEM_CDM_CONSISTENT)
+    throw std::invalid_argument("unknown scheme");
+  if (o.scheme != IBFEM_CDM && o.precision != IBFEM_FP64)
+    throw std::invalid_argument("IMEX and the consistent-mass CDM run in FP64 (precision must be IBFEM_FP64)");
+  in.need_consistent_mass = o.scheme != IBFEM_CDM;
   if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
       o.precision != IBFEM_BF16_TC)
     throw std::invalid_argument("precision not supported by this build");
@@ -570,9 +580,11 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   }
   if (!o.host_only) check_shape_supported(in.dim, in.p, in.physics, o.precision);
   h->setup = build_setup(in);
-  if (o.scheme == IBFEM_IMEX) {
+  if (o.scheme != IBFEM_CDM) {
     imex_partition(h->setup, h->imex_host);
-    h->imex = h->imex_host.n_c > 0;   // without cut cells IMEX is the CDM
+    h->imex = h->imex_host.n_c > 0;   // without cut cells both are the CDM
+    h->consistent = o.scheme == IBFEM_CDM_CONSISTENT;
+    h->beta = h->consistent ? 0.0 : 0.25;
   }
   if (!o.host_only) attach_device(h.get());
   *out = h.release();
@@ -832,9 +844,11 @@ int ibfem_set_dt(ibfem_t* h, double dt) {
     // c-DOFs carry -(c + 1): the fused kernel then forms the Newmark predictor there
     for (int64_t ci = 0; ci < h->imex_host.n_c; ++ci) minv[h->imex_host.c_dof[ci]] = -(double)(ci + 1);
     std::string err;
-    const double beta = 0.25, gamma = 0.5;
-    if (!imex_factor(s, beta * dt * dt, h->imex_host, err)) throw std::runtime_error("IMEX factorisation: " + err);
-    h->imex_upload_factor();
+    const double beta = h->beta, gamma = 0.5;
+    if (!h->consistent) {   // S = M^cc + beta dt^2 K^cc (the consistent-mass S was factored at setup)
+      if (!imex_factor(s, beta * dt * dt, h->imex_host, err)) throw std::runtime_error("IMEX factorisation: " + err);
+      h->imex_upload_factor();
+    }
     h->imex_dev.beta_dt2 = beta * dt * dt;
     h->imex_dev.gamma_dt = gamma * dt;
     h->dev.imex_c1 = (0.5 - beta) * dt * dt;
@@ -1081,9 +1095,10 @@ int ibfem_crit_dt(ibfem_t* h, int max_iter, double rtol, double* dt_crit, double
   // start vector v_i = 1 + 0.5 sin(i) over kept DOFs, normalised
   std::vector<double> v(s.n_dof);
   double nrm = 0;
+  const bool gen = h->consistent && h->imex;   // M = diag(M_L^dd) + consistent M^cc
   for (int64_t i = 0; i < s.n_dof; ++i) {
     v[i] = 1.0 + 0.5 * std::sin((double)i);
-    if (h->imex) {
+    if (h->imex && !gen) {
       int64_t lat = s.lat_of_kept[i / s.ncomp] * s.ncomp + i % s.ncomp;
       if (h->imex_host.c_of_dof[lat] >= 0) v[i] = 0.0;   // explicit (d) block only
     }
@@ -1105,9 +1120,27 @@ int ibfem_crit_dt(ibfem_t* h, int max_iter, double rtol, double* dt_crit, double
   while (it < max_iter && !converged) {
     int chunk = std::min(kPowerChunk, max_iter - it);
     for (int c = 0; c < chunk; ++c) {
-      OpInput x{bufs[b], h->dev.sinv, inv_norm};
-      check(launch_cut_apply_fp64(h->dev, x, false, h->stream), "cut_apply");
-      check(launch_op_fp64(h->dev, x, bufs[1 - b], kModePower, h->partials, h->stream), "power");
+      if (gen) {
+        // power iteration on G^{-1} K G^{-T}, G = diag(sqrt(M_L^dd)) + (c block) P^T L with
+        // M^cc = P^T L L^T P: y = G^{-T} x, z = K y, w = G^{-1} z, lambda ~ x . w
+        if (!h->pw[0]) {
+          h->pw[0] = static_cast<double*>(h->dalloc(s.n_lat_dof * sizeof(double)));
+          h->pw[1] = static_cast<double*>(h->dalloc(s.n_lat_dof * sizeof(double)));
+        }
+        double *y = h->pw[0], *z = h->pw[1];
+        check(launch_scale_vec(s.n_lat_dof, h->dev.sinv, bufs[b], inv_norm, y, h->stream), "scale");
+        check(launch_imex_tri(h->imex_dev, bufs[b], inv_norm, y, true, h->stream), "backward solve");
+        OpInput yi{y, nullptr, nullptr};
+        check(launch_cut_apply_fp64(h->dev, yi, false, h->stream), "cut_apply");
+        check(launch_op_fp64(h->dev, yi, z, kModeApply, nullptr, h->stream), "apply");
+        check(launch_scale_vec(s.n_lat_dof, h->dev.sinv, z, nullptr, bufs[1 - b], h->stream), "scale");
+        check(launch_imex_tri(h->imex_dev, z, nullptr, bufs[1 - b], false, h->stream), "forward solve");
+        check(launch_dot2(s.n_lat_dof, bufs[b], inv_norm, bufs[1 - b], h->partials, h->n_blocks, h->stream), "dot");
+      } else {
+        OpInput x{bufs[b], h->dev.sinv, inv_norm};
+        check(launch_cut_apply_fp64(h->dev, x, false, h->stream), "cut_apply");
+        check(launch_op_fp64(h->dev, x, bufs[1 - b], kModePower, h->partials, h->stream), "power");
+      }
       check(launch_reduce_power(h->partials, h->n_blocks, h->lam_hist, inv_norm, c, h->stream), "reduce");
       b ^= 1;
     }

@@ -34,6 +34,10 @@ struct Handle {
   int tc_scheme() const { return opt.precision == IBFEM_EXACT_TC ? 0 : (opt.precision == IBFEM_BF16X3_TC ? 1 : 2); }
   // IMEX (Algorithm 2): host partition/factor and their device copies
   bool imex = false;
+  bool consistent = false;      // IBFEM_CDM_CONSISTENT: the IMEX machinery with beta = 0
+  double beta = 0.25;
+  double* pw[2] = {nullptr, nullptr};   // work vectors of the consistent-mass power iteration
+  void prepare_consistent();
   ImexData imex_host;
   ImexDev imex_dev{};
   size_t imex_nnz_alloc = 0;

@@ -19,7 +19,8 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_GEOMETRY, ERR_EIG
 GEOM_NONE, GEOM_HOLES, GEOM_VOXELS, GEOM_ROTATED_BOX = 0, 1, 2, 3
 STAB_NONE, STAB_EVS, STAB_MASS_SCALING = 0, 1, 2
 SCALAR, ELASTIC_PLANE_STRAIN = 0, 1
-CDM, IMEX = 0, 1
+CDM, IMEX, CDM_CONSISTENT = 0, 1, 2
+SCHEMES = {"cdm": CDM, "imex": IMEX, "cdm_consistent": CDM_CONSISTENT}
 FP64, EXACT_TC, BF16X3_TC, BF16_TC = 0, 1, 2, 3
 SRC_NONE, SRC_POINT, SRC_EDGE_TRACTION, SRC_GAUSS = 0, 1, 2, 3
 
@@ -173,7 +174,7 @@ class Solver:
         o = Options()
         o.physics = SCALAR if physics == "scalar" else ELASTIC_PLANE_STRAIN
         o.rho, o.c, o.E, o.nu = rho, c, E, nu
-        o.scheme = CDM if scheme == "cdm" else IMEX
+        o.scheme = SCHEMES[scheme]
         o.precision = PRECISIONS[precision]
         o.stream = stream
         o.device = device

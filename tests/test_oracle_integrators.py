@@ -5,6 +5,8 @@ import numpy as np
 import pytest
 
 from oracle import eigen, integrators as I
+from oracle import integrators as OI
+import scipy.linalg as sla
 from oracle.basis import gll_points
 from oracle.discretization import Discretization, source_vector
 from oracle.geometry import Holes
@@ -169,3 +171,64 @@ def test_observer_interpolation_exact_for_polynomials():
     pts = np.array([[0.13, 0.71], [0.25, 0.25], [0.9, 0.05], [0.0, 1.0]])
     O = d.observer_matrix(pts)
     np.testing.assert_allclose(O @ u, f(pts[:, 0], pts[:, 1]), atol=1e-12)
+
+
+# ---------------------------------------------------------------- consistent-mass CDM
+def _mixed_mass(d):
+    """diag(M_L) on the d-DOFs, the consistent block M^cc on the DOFs of cut cells."""
+    import scipy.sparse as sp
+    c = d.c_dofs()
+    Mc = d.consistent_mass().tocsr()
+    mask = np.zeros(d.n_dof, bool)
+    mask[c] = True
+    Dd = sp.diags(np.where(mask, 0.0, d.ML))
+    Cc = sp.diags(mask.astype(float)) @ Mc @ sp.diags(mask.astype(float))
+    return (Dd + Cc).tocsr(), c
+
+
+def _direct_consistent_cdm(K, M, dt, steps, F, f_e):
+    """u_{k+1} = 2 u_k - u_{k-1} + dt^2 M^{-1} (F_k - K u_k), u_{-1} from v_0 = 0 (Eq. cdm
+    with a non-diagonal mass)."""
+    import scipy.sparse.linalg as spla
+    from oracle.discretization import ricker
+    lu = spla.splu(M.tocsc())
+    n = K.shape[0]
+    u = np.zeros(n)
+    up = u + 0.5 * dt * dt * lu.solve(F * ricker(0.0, f_e) - K @ u)
+    for k in range(steps):
+        un = 2.0 * u - up + dt * dt * lu.solve(F * ricker(k * dt, f_e) - K @ u)
+        up, u = u, un
+    return u
+
+
+def test_imex_with_beta_zero_is_the_consistent_mass_cdm():
+    from oracle import discretization as OD
+    from paper_2501_19013_gb300 import workloads as W
+    w = W.plate_holes_imex(n=12, p=2, count=2, seed=3, steps=80).with_(alpha=1e-3)
+    d = OD.from_workload(w)
+    M, c = _mixed_mass(d)
+    lam = sla.eigh(d.K.toarray(), M.toarray(), eigvals_only=True).max()
+    dt = 0.9 * 2.0 / math.sqrt(lam)
+    F = OD.source_vector(d, w.source)
+    sys_ = OI.ImexSystem(d.K, d.ML, d.consistent_mass(), c, dt, beta=0.0)
+    u_imex, _ = OI.imex(sys_, w.steps, F=F, f_e=w.f0)
+    u_cdm = _direct_consistent_cdm(d.K, M, dt, w.steps, F, w.f0)
+    assert np.linalg.norm(u_imex - u_cdm) <= 1e-11 * np.linalg.norm(u_cdm)
+
+
+def test_consistent_mass_cdm_stability_limit():
+    from oracle import discretization as OD
+    from paper_2501_19013_gb300 import workloads as W
+    w = W.plate_holes_imex(n=10, p=2, count=2, seed=3).with_(alpha=1e-3)
+    d = OD.from_workload(w)
+    M, c = _mixed_mass(d)
+    lam = sla.eigh(d.K.toarray(), M.toarray(), eigvals_only=True).max()
+    dtc = 2.0 / math.sqrt(lam)
+    rng = np.random.default_rng(0)
+    u0 = rng.standard_normal(d.n_dof)
+    for f, grows in ((0.99, False), (1.01, True)):
+        sys_ = OI.ImexSystem(d.K, d.ML, d.consistent_mass(), c, f * dtc, beta=0.0)
+        with np.errstate(all="ignore"):
+            u, _ = OI.imex(sys_, 3000, u0=u0)
+            nu = np.linalg.norm(u)
+        assert (not np.isfinite(nu) or nu > 1e3 * np.linalg.norm(u0)) == grows
