@@ -297,12 +297,16 @@ def rotation_zyx(phi: float, theta: float, psi: float) -> np.ndarray:
 
 
 def rotated_cube(ne: int = 13, p: int = 3, alpha: float = 1e-12, stab: str = "evs",
-                 eps: float = 1e-4, quad_depth: int = 3, steps: int = 2000) -> Workload:
+                 eps: float = 1e-4, quad_depth: Optional[int] = None, steps: int = 2000) -> Workload:
     """The paper's benchmark (Sec. 3.1): a cube of edge 0.3 rotated by the Cardan angles
     (10, 10, 10) degrees about the centre of the extended cube [0, 0.5]^3, scalar wave
     (rho = c = 1), a Gaussian volumetric load (sigma = 0.01) centred on one face of the
     cube times a Ricker wavelet (f_e = 10), and the 11 observers of the paper's table of
-    observer locations (source, centre, face, 4 edge centres, 4 corners)."""
+    observer locations (source, centre, face, 4 edge centres, 4 corners).  The quadtree
+    depth of the cut cells defaults to p + 1, which reproduces the paper's critical time
+    steps of the consistent-mass CDM."""
+    if quad_depth is None:
+        quad_depth = p + 1
     lp, le = 0.3, 0.5
     T = rotation_zyx(*(math.radians(10.0),) * 3)
     c = np.full(3, le / 2.0)
