@@ -28,4 +28,4 @@ def test_consistent_mass_dt_crit_matches_the_paper(p, ne, alpha, dt_paper):
     s = ib.from_workload(w, scheme="cdm_consistent")
     dt, lam, it = s.crit_dt(max_iter=3000, rtol=1e-9)
     s.close()
-    assert abs(dt - dt_paper) <= 5e-5 * dt_paper
+    assert abs(dt - dt_paper) <= 2e-4 * dt_paper   # four significant digits
