@@ -221,7 +221,7 @@ def aggregate_replicas(step_ms, n_dof, world, device=None):
 # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, cold cache)
 # of the current kernel code on the benchmark workload; to be re-taken whenever the kernel
 # changes
-MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4"): 76.368128e6 + 2.093312e6}
+MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.368128e6 + 2.093312e6}
 
 # arithmetic of each variant's element operator (the state and the update are FP64 in all)
 DTYPES = {"fp64": "f64",
@@ -259,6 +259,9 @@ def run_ours(args, rank, world, local_rank):
                 dt_crit, lam, it = s.crit_dt(max_iter=2000, rtol=1e-7)
                 dts[key] = w.dt_factor * dt_crit
         dt = dts[key]
+        tile = None
+        if pv == "exact":
+            tile = s.autotune(reps=5)      # tile shape of the exact kernel for this problem
         s.set_dt(dt)
         s.set_initial()
         s.step_timed(args.warmup, flush.data_ptr(), FLUSH_BYTES)
@@ -293,7 +296,9 @@ def run_ours(args, rank, world, local_rank):
         u_end, _ = s.get_state()
         results[prec] = dict(step_ms=step_ms, kernels=kernels, steady_ms=steady_ms, info=info,
                              clocks=clk, run_s=run_s, u_end=u_end, solver=s, wall=t_wall, dt=dt,
-                             run_steps=run_steps, scheme=wv.scheme, stab=wv.stab)
+                             run_steps=run_steps, scheme=wv.scheme, stab=wv.stab,
+                             tile=None if tile is None else {"variant": tile[0], "cells": list(s.info().tile),
+                                                              "autotune_ms_per_apply": [float(x) for x in tile[1]]})
         if prec == "fp64":
             ref_state = u_end
     for prec, r in results.items():
@@ -328,7 +333,8 @@ def run_ours(args, rank, world, local_rank):
         achieved = byts / (kms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         fp64_ops = 2.0 * n_dof          # fma(2, u, -u_prev) and + delta per DOF
-        traffic = MEASURED_TRAFFIC.get((kname, w.name)) if best == "exact" else None
+        variant = rb["tile"]["variant"] if rb.get("tile") else 0
+        traffic = MEASURED_TRAFFIC.get((kname, w.name, variant)) if best == "exact" else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
@@ -367,6 +373,7 @@ def run_ours(args, rank, world, local_rank):
                            "run_steps": r["run_steps"], "dt": r["dt"], "scheme": r["scheme"],
                            "stab": r["stab"], "run_wall_s": r["run_s"],
                            "time_to_accuracy_s": (r["step_ms"] * 1e-3 * r["run_steps"]) if (r["rel_l2"] is not None and r["rel_l2"] <= 1e-4) else None,
+                           "tile": r.get("tile"),
                            "kernels_ms": r["kernels"]}
     launches = args.steps * len(rb["kernels"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -138,6 +138,8 @@ typedef struct {
     int64_t n_cut_matrices;   /* distinct cut-cell matrix sets: equal to n_cut, or fewer
                                  for voxel images with whole voxels per cell, where cut
                                  cells with equal voxel blocks share one set             */
+    int32_t tile_variant;     /* tensor-core tile shape in use (0 full, 1 small)       */
+    int32_t tile[3];          /* cells per tile and axis of the tensor-core kernel     */
 } ibfem_info_t;
 
 /* ---- lifetime -------------------------------------------------------------------- */
@@ -234,6 +236,21 @@ int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells);
 /* Element stiffness (n_loc x n_loc, row-major) used for cell `cell` (shared reference
  * matrix for uncut cells); optional lumped diagonal (n_loc). Errors: ARG (outside).   */
 int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml);
+
+/* ---- tile shape -------------------------------------------------------------------- */
+
+/* The exact tensor-core kernel exists with two tile shapes: variant 0 fills the 128 rows
+ * of one MMA with the halo'd tile (2D: 8x8 cells for n_loc >= 32, else 15x7; 3D: 4x4x4),
+ * variant 1 is smaller (2D: 5x5 or 7x7; 3D: 3x3x3): more tiles for small problems and, in
+ * 3D, less shared memory per CTA.  ibfem_set_tile_variant picks one; ibfem_autotune times
+ * reps operator applications with each (the state is untouched), keeps the faster and
+ * returns its index and both times (ms per application) in ms[2].  The FP64 path and the
+ * BF16 schemes have variant 0 only (ibfem_autotune then returns 0 and zero times).
+ * Results of the two variants agree within the exact scheme's accuracy (the digit
+ * exponent is per tile), not bitwise.  This is a part of this library; the paper has no
+ * counterpart.  Errors: ARG, STATE (batch member), CUDA.                                  */
+int ibfem_set_tile_variant(ibfem_t* h, int variant);
+int ibfem_autotune(ibfem_t* h, int reps, int* variant, double* ms);
 
 /* ---- deferred upload ----------------------------------------------------------------- */
 

@@ -72,7 +72,7 @@ struct Staging {
 constexpr int kStaging = 4;
 
 struct Group {
-  int dim = 0, p = 0, ncomp = 0;
+  int dim = 0, p = 0, ncomp = 0, variant = 0;
   int n_members = 0, total_tiles = 0, cap = 0;
   BatchMember* d_members = nullptr;
   int* d_tile_start = nullptr;
@@ -90,7 +90,7 @@ struct ibfem_batch_s {
   std::vector<Entry> active;
   std::vector<ibfem_t*> finished;
   std::vector<Image> images;
-  std::map<std::tuple<int, int, int>, Group> groups;
+  std::map<std::tuple<int, int, int, int>, Group> groups;   // (dim, p, ncomp, tile variant)
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;   // kGraphSteps batched steps of the current membership
   cudaEvent_t fork = nullptr, mark = nullptr;
@@ -136,9 +136,9 @@ int image_index(ibfem_batch_s* b, const Handle* h) {
 // (so that a CTA rarely reloads K_ref) then by admission; tile ranges as prefix sums.
 void ibfem_batch_s::rebuild() {
   destroy_graph();
-  std::map<std::tuple<int, int, int>, std::vector<const Entry*>> by_shape;
+  std::map<std::tuple<int, int, int, int>, std::vector<const Entry*>> by_shape;
   for (const Entry& e : active)
-    by_shape[std::make_tuple(e.h->setup.dim, e.h->setup.p, e.h->setup.ncomp)].push_back(&e);
+    by_shape[std::make_tuple(e.h->setup.dim, e.h->setup.p, e.h->setup.ncomp, e.h->tc_variant)].push_back(&e);
   for (auto& kv : groups) kv.second.n_members = kv.second.total_tiles = 0;
   for (auto& kv : by_shape) {
     std::vector<const Entry*>& v = kv.second;
@@ -149,6 +149,7 @@ void ibfem_batch_s::rebuild() {
     g.dim = std::get<0>(kv.first);
     g.p = std::get<1>(kv.first);
     g.ncomp = std::get<2>(kv.first);
+    g.variant = std::get<3>(kv.first);
     const int n = (int)v.size();
     if (n > g.cap) {
       // grow the tables; the old ones may still be read by queued launches
@@ -204,7 +205,8 @@ void ibfem_batch_s::rebuild() {
     g.n_members = n;
     g.total_tiles = ts[n];
     // one-time kernel configuration outside any stream capture (launches nothing)
-    check(launch_op_tc_batch(g.dim, g.p, g.ncomp, nullptr, nullptr, 0, 0, nullptr, stream), "batched op_tc setup");
+    check(launch_op_tc_batch(g.dim, g.p, g.ncomp, g.variant, nullptr, nullptr, 0, 0, nullptr, stream),
+          "batched op_tc setup");
   }
   dirty = false;
 }
@@ -216,7 +218,7 @@ void ibfem_batch_s::enqueue_steps(int n) {
     if (g.n_members == 0) continue;
     check(cudaStreamWaitEvent(g.side, fork, 0), "fork wait");
     for (int i = 0; i < n; ++i)
-      check(launch_op_tc_batch(g.dim, g.p, g.ncomp, g.d_members, g.d_tile_start, g.n_members, g.total_tiles,
+      check(launch_op_tc_batch(g.dim, g.p, g.ncomp, g.variant, g.d_members, g.d_tile_start, g.n_members, g.total_tiles,
                                g.d_ctl, g.side),
             "batched op_tc");
     check(cudaEventRecord(g.done, g.side), "join");

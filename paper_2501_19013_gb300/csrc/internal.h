@@ -136,14 +136,16 @@ cudaError_t launch_sample_now(const DevProblem& pb, const double* u, double* out
 int op_fp64_blocks(const DevProblem& pb);
 // Launchers (kernels_tc.cu)
 // scheme: 0 exact digit slices, 1 bf16 hi/lo three-pass, 2 bf16 one pass
-cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme,
+// variant: tile shape (0 full MMA tile, 1 small tile; 1 only with scheme 0)
+cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme, int variant,
                          cudaStream_t st);
 // Batched launch (exact scheme, CDM): every member advances one step; members[m] owns the
 // global tiles [tile_start[m], tile_start[m + 1]).
-cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, const BatchMember* members, const int* tile_start,
-                               int n_members, int total_tiles, BatchCtl* ctl, cudaStream_t st);
+cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, int variant, const BatchMember* members,
+                               const int* tile_start, int n_members, int total_tiles, BatchCtl* ctl,
+                               cudaStream_t st);
 bool op_tc_supported(int dim, int p, int ncomp);
-void op_tc_tiles(int dim, int p, int ncomp, int* tile);
+void op_tc_tiles(int dim, int p, int ncomp, int variant, int* tile);
 void op_tc_dims(int dim, int p, int ncomp, int* kp, int* np);
 int op_tc_core_offset(int kp, int row, int k);
 bool op_fp64_supported(int dim, int p, int ncomp);

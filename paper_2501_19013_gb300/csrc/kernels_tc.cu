@@ -183,11 +183,19 @@ __device__ __forceinline__ void fp64_digits(double x, int em, int d[4]) {
 
 }  // namespace
 
-__host__ __device__ constexpr int tc_tile_x(int dim, int nl) { return dim == 3 ? 4 : (nl >= 32 ? 8 : 15); }
-__host__ __device__ constexpr int tc_tile_y(int dim, int nl) { return dim == 3 ? 4 : (nl >= 32 ? 8 : 7); }
-__host__ __device__ constexpr int tc_tile_z(int dim) { return dim == 3 ? 4 : 1; }
+// Tile shapes (owned cells per axis; the halo adds one cell on the low side of each axis,
+// and the halo'd tile must fit the M = 128 rows of one MMA).  Variant 0 fills the MMA;
+// variant 1 is a smaller tile (more tiles for small problems, less shared memory in 3D);
+// the autotuner picks between them per problem.
+__host__ __device__ constexpr int tc_tile_x(int dim, int nl, int v) {
+  return dim == 3 ? (v ? 3 : 4) : (nl >= 32 ? (v ? 5 : 8) : (v ? 7 : 15));
+}
+__host__ __device__ constexpr int tc_tile_y(int dim, int nl, int v) {
+  return dim == 3 ? (v ? 3 : 4) : (nl >= 32 ? (v ? 5 : 8) : 7);
+}
+__host__ __device__ constexpr int tc_tile_z(int dim, int v) { return dim == 3 ? (v ? 3 : 4) : 1; }
 
-template <int DIM, int P, int NC>
+template <int DIM, int P, int NC, int TILE>
 struct TcCfg {
   static constexpr int NN1 = P + 1;
   static constexpr int NNL = DIM == 2 ? NN1 * NN1 : NN1 * NN1 * NN1;
@@ -196,7 +204,7 @@ struct TcCfg {
   static constexpr int NP = (NL + 15) / 16 * 16;   // N padded (M = 128 needs N % 16 == 0)
   static constexpr int NACC = 4;                    // accumulators (levels 0..3)
   static constexpr int TMEM_COLS = NACC * NP <= 32 ? 32 : (NACC * NP <= 64 ? 64 : (NACC * NP <= 128 ? 128 : (NACC * NP <= 256 ? 256 : 512)));
-  static constexpr int TX = tc_tile_x(DIM, NL), TY = tc_tile_y(DIM, NL), TZ = tc_tile_z(DIM);
+  static constexpr int TX = tc_tile_x(DIM, NL, TILE), TY = tc_tile_y(DIM, NL, TILE), TZ = tc_tile_z(DIM, TILE);
   static constexpr int EX = TX + 1, EY = TY + 1, EZ = DIM == 3 ? TZ + 1 : 1;
   static constexpr int NE = EX * EY * EZ;
   static constexpr int PX = EX * P + 1, PY = EY * P + 1, PZ = DIM == 3 ? EZ * P + 1 : 1;
@@ -238,13 +246,13 @@ __host__ __device__ __forceinline__ int bf16_core_offset(int row, int k) {
 // BATCH: the tiles of several problems (members) of one shape in one launch, CDM mode.  A
 // CTA keeps the descriptor of its current member in shared memory and reloads the K_ref
 // image only when a member with another image comes up (the host orders members by image).
-template <int DIM, int P, int NC, int SCHEME, bool BATCH>
+template <int DIM, int P, int NC, int SCHEME, bool BATCH, int TILE>
 __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ DevProblem pb_arg, const double* u_arg,
                                                     double* out_arg, int mode,
                                                     const BatchMember* __restrict__ members,
                                                     const int* __restrict__ tile_start, int n_members,
                                                     int total_tiles, BatchCtl* ctl) {
-  using C = TcCfg<DIM, P, NC>;
+  using C = TcCfg<DIM, P, NC, TILE>;
   constexpr int NL = C::NL, NN1 = C::NN1, KP = C::KP, NP = C::NP;
   constexpr int EX = C::EX, EY = C::EY, PX = C::PX, PY = C::PY;
   constexpr int NV = C::PATCH;                                // patch values
@@ -900,12 +908,12 @@ bool op_tc_supported(int dim, int p, int ncomp) {
   return false;
 }
 
-void op_tc_tiles(int dim, int p, int ncomp, int* t) {
+void op_tc_tiles(int dim, int p, int ncomp, int variant, int* t) {
   int nl = ncomp;
   for (int k = 0; k < dim; ++k) nl *= p + 1;
-  t[0] = tc_tile_x(dim, nl);
-  t[1] = tc_tile_y(dim, nl);
-  t[2] = tc_tile_z(dim);
+  t[0] = tc_tile_x(dim, nl, variant);
+  t[1] = tc_tile_y(dim, nl, variant);
+  t[2] = tc_tile_z(dim, variant);
 }
 
 void op_tc_dims(int dim, int p, int ncomp, int* kp, int* np) {
@@ -945,50 +953,58 @@ static int tc_configure(KernelT kernel, size_t smem_launch, int tmem_max) {
   return per_sm * sms;
 }
 
-template <int D, int P, int N, int S>
+template <int D, int P, int N, int S, int T>
 static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* out, int mode, cudaStream_t st) {
-  using C = TcCfg<D, P, N>;
+  using C = TcCfg<D, P, N, T>;
   // thread-safe one-time configuration (function-local static initialisation)
-  static const int resident = tc_configure(op_tc_kernel<D, P, N, S, false>, C::SMEM_LAUNCH, C::CTA_TMEM_MAX);
+  static const int resident = tc_configure(op_tc_kernel<D, P, N, S, false, T>, C::SMEM_LAUNCH, C::CTA_TMEM_MAX);
   if (resident == 0) return cudaErrorInvalidConfiguration;
   int tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
   int blocks = std::min(tiles, resident);
-  op_tc_kernel<D, P, N, S, false><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode, nullptr, nullptr, 0, 0,
-                                                                      nullptr);
+  op_tc_kernel<D, P, N, S, false, T><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode, nullptr, nullptr, 0, 0,
+                                                                         nullptr);
   return cudaGetLastError();
 }
 
-template <int D, int P, int N>
+template <int D, int P, int N, int T>
 static cudaError_t launch_tc_batch_t(const BatchMember* members, const int* tile_start, int n_members,
                                      int total_tiles, BatchCtl* ctl, cudaStream_t st) {
-  using C = TcCfg<D, P, N>;
+  using C = TcCfg<D, P, N, T>;
   constexpr size_t smem = std::max(C::SMEM + (sizeof(BatchMember) + 15) / 16 * 16, C::SMEM_FLOOR);
-  static const int resident = tc_configure(op_tc_kernel<D, P, N, 0, true>, smem, C::CTA_TMEM_MAX);
+  static const int resident = tc_configure(op_tc_kernel<D, P, N, 0, true, T>, smem, C::CTA_TMEM_MAX);
   if (resident == 0) return cudaErrorInvalidConfiguration;
   if (total_tiles <= 0) return cudaSuccess;
   int blocks = std::min(total_tiles, resident);
   DevProblem none{};
-  op_tc_kernel<D, P, N, 0, true><<<blocks, 256, smem, st>>>(none, nullptr, nullptr, kModeCDM, members, tile_start,
-                                                            n_members, total_tiles, ctl);
+  op_tc_kernel<D, P, N, 0, true, T><<<blocks, 256, smem, st>>>(none, nullptr, nullptr, kModeCDM, members, tile_start,
+                                                               n_members, total_tiles, ctl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, const BatchMember* members, const int* tile_start,
-                               int n_members, int total_tiles, BatchCtl* ctl, cudaStream_t st) {
-#define X(D, P, N) \
-  if (dim == D && p == P && ncomp == N) return launch_tc_batch_t<D, P, N>(members, tile_start, n_members, total_tiles, ctl, st);
+cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, int variant, const BatchMember* members,
+                               const int* tile_start, int n_members, int total_tiles, BatchCtl* ctl,
+                               cudaStream_t st) {
+#define X(D, P, N)                                                                                       \
+  if (dim == D && p == P && ncomp == N) {                                                                \
+    if (variant == 1) return launch_tc_batch_t<D, P, N, 1>(members, tile_start, n_members, total_tiles, ctl, st); \
+    return launch_tc_batch_t<D, P, N, 0>(members, tile_start, n_members, total_tiles, ctl, st);          \
+  }
   IBFEM_TC_SHAPES(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme,
+// the small tile (variant 1) exists for the exact scheme, which is the one the batch and
+// the serving loop run
+cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme, int variant,
                          cudaStream_t st) {
-#define X(D, P, N)                                                               \
-  if (pb.dim == D && pb.p == P && pb.ncomp == N) {                               \
-    if (scheme == 0) return launch_tc_t<D, P, N, 0>(pb, u, out, mode, st);       \
-    if (scheme == 1) return launch_tc_t<D, P, N, 1>(pb, u, out, mode, st);       \
-    return launch_tc_t<D, P, N, 2>(pb, u, out, mode, st);                        \
+#define X(D, P, N)                                                                 \
+  if (pb.dim == D && pb.p == P && pb.ncomp == N) {                                 \
+    if (scheme == 0 && variant == 1) return launch_tc_t<D, P, N, 0, 1>(pb, u, out, mode, st); \
+    if (variant != 0) return cudaErrorInvalidValue;                                \
+    if (scheme == 0) return launch_tc_t<D, P, N, 0, 0>(pb, u, out, mode, st);      \
+    if (scheme == 1) return launch_tc_t<D, P, N, 1, 0>(pb, u, out, mode, st);      \
+    return launch_tc_t<D, P, N, 2, 0>(pb, u, out, mode, st);                       \
   }
   IBFEM_TC_SHAPES(X)
 #undef X

@@ -231,33 +231,81 @@ void Handle::build_device() {
       }
     d_minv32 = upload(m32);
     pb.minv32 = d_minv32;
-    op_tc_tiles(s.dim, s.p, s.ncomp, tc_tile);
-    for (int k = 0; k < 3; ++k) pb.tc_tiles[k] = k < s.dim ? (s.n[k] + tc_tile[k] - 1) / tc_tile[k] : 1;
-    // processing order of the tiles: the persistent kernel hands tiles out in this order,
-    // so the slow ones (cut cells of the halo'd tile run on the CUDA cores, one warp per
-    // cell, eight at a time) start first and short tiles fill the end of the step
-    const int ntx = pb.tc_tiles[0], nty = pb.tc_tiles[1], ntz = pb.tc_tiles[2];
-    std::vector<int> ncut_tile((size_t)ntx * nty * ntz, 0);
-    for (int t = 0; t < ntx * nty * ntz; ++t) {
-      const int bx = t % ntx, by = (t / ntx) % nty, bz = t / (ntx * nty);
-      int c = 0;
-      for (int ez = (s.dim == 3 ? bz * tc_tile[2] - 1 : 0); ez < (s.dim == 3 ? (bz + 1) * tc_tile[2] : 1); ++ez)
-        for (int ey = by * tc_tile[1] - 1; ey < (by + 1) * tc_tile[1]; ++ey)
-          for (int ex = bx * tc_tile[0] - 1; ex < (bx + 1) * tc_tile[0]; ++ex) {
-            if (ex < 0 || ey < 0 || ez < 0 || ex >= s.n[0] || ey >= s.n[1] || (s.dim == 3 && ez >= s.n[2])) continue;
-            if (s.cls[((int64_t)ez * s.n[1] + ey) * s.n[0] + ex] == kCut) ++c;
-          }
-      ncut_tile[t] = (c + 7) / 8;   // rounds of eight warps
-    }
-    std::vector<int32_t> order(ncut_tile.size());
-    for (size_t t = 0; t < order.size(); ++t) order[t] = (int32_t)t;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return ncut_tile[a] > ncut_tile[b]; });
-    pb.tc_order = upload(order);
+    build_tc_tiles();
   }
   scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
   lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
   scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
   check(cudaStreamSynchronize(stream), "setup sync");
+}
+
+// tile grid of the tensor-core kernel for the current tile variant and the processing
+// order of its tiles: the persistent kernel hands tiles out in this order, so the slow ones
+// (cut cells of the halo'd tile run on the CUDA cores, one warp per cell, eight at a time)
+// start first and short tiles fill the end of the step
+void Handle::build_tc_tiles() {
+  const Setup& s = setup;
+  DevProblem& pb = dev;
+  op_tc_tiles(s.dim, s.p, s.ncomp, tc_variant, tc_tile);
+  for (int k = 0; k < 3; ++k) pb.tc_tiles[k] = k < s.dim ? (s.n[k] + tc_tile[k] - 1) / tc_tile[k] : 1;
+  const int ntx = pb.tc_tiles[0], nty = pb.tc_tiles[1], ntz = pb.tc_tiles[2];
+  std::vector<int> ncut_tile((size_t)ntx * nty * ntz, 0);
+  for (int t = 0; t < ntx * nty * ntz; ++t) {
+    const int bx = t % ntx, by = (t / ntx) % nty, bz = t / (ntx * nty);
+    int c = 0;
+    for (int ez = (s.dim == 3 ? bz * tc_tile[2] - 1 : 0); ez < (s.dim == 3 ? (bz + 1) * tc_tile[2] : 1); ++ez)
+      for (int ey = by * tc_tile[1] - 1; ey < (by + 1) * tc_tile[1]; ++ey)
+        for (int ex = bx * tc_tile[0] - 1; ex < (bx + 1) * tc_tile[0]; ++ex) {
+          if (ex < 0 || ey < 0 || ez < 0 || ex >= s.n[0] || ey >= s.n[1] || (s.dim == 3 && ez >= s.n[2])) continue;
+          if (s.cls[((int64_t)ez * s.n[1] + ey) * s.n[0] + ex] == kCut) ++c;
+        }
+    ncut_tile[t] = (c + 7) / 8;   // rounds of eight warps
+  }
+  std::vector<int32_t> order(ncut_tile.size());
+  for (size_t t = 0; t < order.size(); ++t) order[t] = (int32_t)t;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return ncut_tile[a] > ncut_tile[b]; });
+  pb.tc_order = upload(order);
+}
+
+// the load CSR over the tensor-core tiles (rebuilt when the tile variant changes)
+void Handle::upload_tc_sources() {
+  const Setup& s = setup;
+  const int nt = dev.tc_tiles[0] * dev.tc_tiles[1] * dev.tc_tiles[2];
+  std::vector<std::vector<std::pair<int64_t, double>>> per2(nt);
+  for (auto& e : src_host) {
+    int64_t rem = e.first / s.ncomp;
+    int t = 0, stride = 1;
+    for (int k = 0; k < s.dim; ++k) {
+      int64_t g = rem % s.lat[k];
+      rem /= s.lat[k];
+      int b = (int)std::min<int64_t>(g / ((int64_t)tc_tile[k] * s.p), dev.tc_tiles[k] - 1);
+      t += b * stride;
+      stride *= dev.tc_tiles[k];
+    }
+    per2[t].push_back(e);
+  }
+  std::vector<int32_t> p2(nt + 1, 0);
+  std::vector<int64_t> d2;
+  std::vector<double> v2;
+  for (int t = 0; t < nt; ++t) {
+    for (auto& e : per2[t]) {
+      d2.push_back(e.first);
+      v2.push_back(e.second);
+    }
+    p2[t + 1] = (int32_t)d2.size();
+  }
+  dev.tsrc_ptr = upload(p2);
+  dev.tsrc_dof = upload(d2);
+  dev.tsrc_val = upload(v2);
+}
+
+void Handle::set_tc_variant(int v) {
+  if (v == tc_variant) return;
+  tc_variant = v;
+  build_tc_tiles();
+  if (dev.tsrc_ptr) upload_tc_sources();
+  invalidate_graphs();
+  check(cudaStreamSynchronize(stream), "tile variant");
 }
 
 size_t Handle::planned_device_bytes() const {
@@ -287,7 +335,7 @@ size_t Handle::planned_device_bytes() const {
     op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
     b += 4 * (size_t)kp * np * 2 + arr(np, 4);            // K_ref image, row exponents
     int tt[3] = {1, 1, 1};
-    op_tc_tiles(s.dim, s.p, s.ncomp, tt);
+    op_tc_tiles(s.dim, s.p, s.ncomp, tc_variant, tt);
     int64_t ntc = 1;
     for (int k = 0; k < s.dim; ++k) ntc *= (s.n[k] + tt[k] - 1) / tt[k];
     b += arr(ntc, 4);                                     // tile order
@@ -391,7 +439,7 @@ void Handle::enqueue_step(int cur) {
     slot_name[1] = tc_scheme() == 0 ? "op_tc_exact_fused_cdm" : (tc_scheme() == 1 ? "op_tc_bf16x3_fused_cdm" : "op_tc_bf16_fused_cdm");
     if (timing) step_first_ev.push_back(ev_used);
     timed_begin(1);
-    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_scheme(), stream), "op_tc");
+    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_scheme(), tc_variant, stream), "op_tc");
     timed_end();
     if (timing) step_last_ev.push_back(ev_used - 1);
     return;
@@ -653,6 +701,8 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
   }
   out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes;
   out->n_cut_matrices = s.n_cut_mat;
+  out->tile_variant = h->tc_variant;
+  for (int k = 0; k < 3; ++k) out->tile[k] = h->tc_tile[k];
   return IBFEM_OK;
 }
 
@@ -760,35 +810,7 @@ int ibfem_set_source(ibfem_t* h, int kind, const double* params, int nparams, do
   h->dev.src_ptr = h->upload(ptr);
   h->dev.src_dof = h->upload(sd);
   h->dev.src_val = h->upload(sv);
-  if (h->opt.precision != IBFEM_FP64) {
-    int nt = h->dev.tc_tiles[0] * h->dev.tc_tiles[1] * h->dev.tc_tiles[2];
-    std::vector<std::vector<std::pair<int64_t, double>>> per2(nt);
-    for (auto& e : merged) {
-      int64_t rem = e.first / s.ncomp;
-      int t = 0, stride = 1;
-      for (int k = 0; k < s.dim; ++k) {
-        int64_t g = rem % s.lat[k];
-        rem /= s.lat[k];
-        int b = (int)std::min<int64_t>(g / ((int64_t)h->tc_tile[k] * s.p), h->dev.tc_tiles[k] - 1);
-        t += b * stride;
-        stride *= h->dev.tc_tiles[k];
-      }
-      per2[t].push_back(e);
-    }
-    std::vector<int32_t> p2(nt + 1, 0);
-    std::vector<int64_t> d2;
-    std::vector<double> v2;
-    for (int t = 0; t < nt; ++t) {
-      for (auto& e : per2[t]) {
-        d2.push_back(e.first);
-        v2.push_back(e.second);
-      }
-      p2[t + 1] = (int32_t)d2.size();
-    }
-    h->dev.tsrc_ptr = h->upload(p2);
-    h->dev.tsrc_dof = h->upload(d2);
-    h->dev.tsrc_val = h->upload(v2);
-  }
+  if (h->opt.precision != IBFEM_FP64) h->upload_tc_sources();
   h->dev.f_e = kind == IBFEM_SRC_NONE ? 0.0 : f_e;
   h->invalidate_graphs();
   check(cudaStreamSynchronize(h->stream), "source upload");
@@ -1073,7 +1095,7 @@ int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
   check(cudaMemcpyAsync(h->W, lx.data(), lx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "x");
   OpInput in{h->W, nullptr, nullptr};
   if (h->opt.precision != IBFEM_FP64) {
-    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_scheme(), h->stream), "apply_tc");
+    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_scheme(), h->tc_variant, h->stream), "apply_tc");
   } else {
     check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
     check(launch_op_fp64(h->dev, in, h->scratch, kModeApply, nullptr, h->stream), "apply");
@@ -1081,6 +1103,59 @@ int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
   check(cudaMemcpyAsync(lx.data(), h->scratch, lx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "y");
   check(cudaStreamSynchronize(h->stream), "apply sync");
   h->from_lattice(lx, y);
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_set_tile_variant(ibfem_t* h, int variant) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (variant != 0 && variant != 1) return fail(IBFEM_ERR_ARG, "tile variant must be 0 or 1");
+  if (variant == 1 && h->tc_scheme() != 0)
+    return fail(IBFEM_ERR_ARG, "the small tile exists for the exact tensor-core path (IBFEM_EXACT_TC)");
+  if (h->opt.precision == IBFEM_FP64) return variant == 0 ? IBFEM_OK : fail(IBFEM_ERR_ARG, "FP64 path has one tile shape");
+  IBFEM_TRY
+  h->set_tc_variant(variant);
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
+int ibfem_autotune(ibfem_t* h, int reps, int* variant, double* ms) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (reps < 1) return fail(IBFEM_ERR_ARG, "reps must be >= 1");
+  IBFEM_TRY
+  double t[2] = {0.0, 0.0};
+  int best = 0;
+  if (h->opt.precision != IBFEM_FP64 && h->tc_scheme() == 0) {
+    // time reps operator applications (the step's kernel in apply mode, on work vectors:
+    // the state is untouched) with each tile shape, after two untimed ones
+    cudaEvent_t e0, e1;
+    check(cudaEventCreate(&e0), "event");
+    check(cudaEventCreate(&e1), "event");
+    for (int v = 0; v < 2; ++v) {
+      h->set_tc_variant(v);
+      for (int i = 0; i < 2; ++i)
+        check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, 0, v, h->stream), "autotune");
+      check(cudaEventRecord(e0, h->stream), "event");
+      for (int i = 0; i < reps; ++i)
+        check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, 0, v, h->stream), "autotune");
+      check(cudaEventRecord(e1, h->stream), "event");
+      check(cudaEventSynchronize(e1), "event");
+      float f = 0.f;
+      check(cudaEventElapsedTime(&f, e0, e1), "event");
+      t[v] = f / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best = t[1] < t[0] ? 1 : 0;
+    h->set_tc_variant(best);
+  }
+  if (variant) *variant = best;
+  if (ms) {
+    ms[0] = t[0];
+    ms[1] = t[1];
+  }
   return IBFEM_OK;
   IBFEM_CATCH
 }

@@ -30,6 +30,10 @@ struct Handle {
   double* d_minv = nullptr;
   float* d_minv32 = nullptr;
   int tc_tile[3] = {1, 1, 1};
+  int tc_variant = 0;          // tile shape of the tensor-core kernel (0 full, 1 small)
+  void build_tc_tiles();
+  void upload_tc_sources();
+  void set_tc_variant(int v);
   // tensor-core scheme: 0 exact digit slices, 1 bf16 three-pass, 2 bf16 one pass
   int tc_scheme() const { return opt.precision == IBFEM_EXACT_TC ? 0 : (opt.precision == IBFEM_BF16X3_TC ? 1 : 2); }
   // IMEX (Algorithm 2): host partition/factor and their device copies

@@ -64,7 +64,7 @@ class Info(C.Structure):
                 ("n_loc", C.c_int32), ("ncomp", C.c_int32), ("precision", C.c_int32),
                 ("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double),
                 ("lambda_ref", C.c_double), ("device_bytes", C.c_size_t),
-                ("n_cut_matrices", C.c_int64)]
+                ("n_cut_matrices", C.c_int64), ("tile_variant", C.c_int32), ("tile", C.c_int32 * 3)]
 
 
 _lib = None
@@ -105,6 +105,8 @@ def lib():
         "ibfem_apply_operator_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
         "ibfem_upload": (C.c_int, [vp]),
+        "ibfem_set_tile_variant": (C.c_int, [vp, C.c_int]),
+        "ibfem_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), DP]),
         "ibfem_batch_create": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
         "ibfem_batch_add": (C.c_int, [vp, vp, C.c_int64]),
         "ibfem_batch_run": (C.c_int, [vp, C.c_int64]),
@@ -226,6 +228,16 @@ class Solver:
     def upload(self):
         """Move a host-only handle onto its device (``ibfem_upload``)."""
         _check(lib().ibfem_upload(self.h))
+
+    def set_tile_variant(self, variant):
+        _check(lib().ibfem_set_tile_variant(self.h, int(variant)))
+
+    def autotune(self, reps=5):
+        """Time both tile shapes and keep the faster: (variant, [ms variant 0, ms variant 1])."""
+        v = C.c_int()
+        ms = np.zeros(2)
+        _check(lib().ibfem_autotune(self.h, int(reps), C.byref(v), _dp(ms)))
+        return v.value, ms
 
     def info(self):
         i = Info()

@@ -48,6 +48,7 @@ class Request:
     footprint: int = 0
     n_dof: int = 0
     dt: float = math.nan
+    tile_variant: int = 0
     error: Optional[str] = None
     result: Any = None
 
@@ -239,7 +240,8 @@ class TcBackend(Backend):
     """GPU backend: exact tensor-core solvers in one ``ibfem`` batch."""
 
     def __init__(self, device: int = 0, dt_factor: float = 0.9, keep_state: bool = False,
-                 dt_fn: Optional[Callable[[Any], float]] = None):
+                 dt_fn: Optional[Callable[[Any], float]] = None, autotune: bool = True):
+        import threading
         from . import ibfem
         self.ib = ibfem
         self.batch = ibfem.Batch(device=device)
@@ -247,6 +249,9 @@ class TcBackend(Backend):
         self.dt_factor = dt_factor
         self.keep_state = keep_state
         self.dt_fn = dt_fn
+        self.autotune = autotune
+        self.tiles = {}                  # (dim, cells, p, physics) -> tile variant
+        self.tiles_lock = threading.Lock()
 
     def setup(self, r: Request):
         w = r.workload
@@ -259,6 +264,18 @@ class TcBackend(Backend):
     def init(self, r: Request, s) -> None:
         w = r.workload
         s.upload()
+        if self.autotune:
+            # tile shape by the autotuner, once per problem shape (later ones reuse it)
+            key = (w.dim, tuple(w.n), w.p, w.physics)
+            with self.tiles_lock:
+                v = self.tiles.get(key)
+            if v is None:
+                v, _ = s.autotune(reps=3)
+                with self.tiles_lock:
+                    self.tiles[key] = v
+            else:
+                s.set_tile_variant(v)
+            r.tile_variant = v
         if self.dt_fn is not None:
             dt = self.dt_fn(s)
         else:

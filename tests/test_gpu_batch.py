@@ -38,8 +38,9 @@ def _prepared(w, dt=None, capacity=None):
     return s, dt
 
 
-def _alone(w, dt, steps):
+def _alone(w, dt, steps, variant=0):
     s, _ = _prepared(w, dt, steps + 1)
+    s.set_tile_variant(variant)
     s.step(steps)
     s.sync()
     u, up = s.get_state()
@@ -142,7 +143,42 @@ def test_server_results_equal_alone():
     assert summ["p50_s"] > 0 and summ["p99_s"] >= summ["p50_s"]
     for r in st.requests:
         ser, u = r.result
-        ua, _, sera = _alone(r.workload, r.dt, r.steps)
+        ua, _, sera = _alone(r.workload, r.dt, r.steps, r.tile_variant)
         assert np.array_equal(u, ua), r.workload.name
         if ser is not None:
             assert np.array_equal(ser, sera), r.workload.name
+
+
+def test_batch_mixes_tile_variants_and_equals_alone():
+    """Members of one shape class with different tile shapes run as separate launches of the
+    batch; each equals its own single-problem run bitwise."""
+    from paper_2501_19013_gb300 import ibfem as ib
+    cases = [_cases()[0], _cases()[0].with_(steps=90), _cases()[5]]
+    variants = [0, 1, 1]
+    members = []
+    for w, v in zip(cases, variants):
+        s, dt = _prepared(w)
+        s.set_tile_variant(v)
+        members.append((s, dt))
+    b = ib.Batch()
+    for (s, _), w in zip(members, cases):
+        b.add(s, w.steps)
+    done = []
+    for _ in range(60):
+        b.run(32)
+        done += b.poll()
+        if len(done) == len(cases):
+            break
+    assert len(done) == len(cases)
+    for (s, dt), w, v in zip(members, cases, variants):
+        s.sync()
+        u, _ = s.get_state()
+        a, _ = _prepared(w, dt, w.steps + 1)
+        a.set_tile_variant(v)
+        a.step(w.steps)
+        a.sync()
+        ua, _ = a.get_state()
+        a.close()
+        assert np.array_equal(u, ua), (w.name, v)
+        s.close()
+    b.close()

@@ -66,3 +66,38 @@ def test_fp32_accumulating_schemes_run(prec):
     dt = oracle_dt(d)
     u_g, _, _ = gpu_cdm(w, dt, w.steps, precision=prec)
     assert np.isfinite(u_g).all()
+
+
+# ---------------------------------------------------------------- small tile (variant 1)
+@pytest.mark.parametrize("case", TC_CASES + ["rotated_cube_gauss"])
+def test_small_tile_variant_apply_and_run(case):
+    """The exact kernel with the small tile: K x within the exact tolerance and a CDM run
+    within the mixed bar against the oracle."""
+    w = SMALL_CASES[case]()
+    d = oracle_disc(w)
+    s = gpu_solver(w, precision="exact")
+    s.set_tile_variant(1)
+    inf = s.info()
+    assert inf.tile_variant == 1
+    x = np.random.default_rng(1).standard_normal(d.n_dof)
+    assert rel_l2(s.apply_operator(x), d.K @ x) < APPLY_TOL["exact"]
+    dt = oracle_dt(d)
+    u_o, _, _ = oracle_cdm(w, d, dt, w.steps)
+    s.set_dt(dt)
+    s.set_initial()
+    s.step(w.steps)
+    s.sync()
+    u_g, _ = s.get_state()
+    s.close()
+    assert rel_l2(u_g, u_o) <= MIXED_BAR
+
+
+def test_autotune_picks_the_faster_variant():
+    from paper_2501_19013_gb300 import workloads as W
+    w = W.plate_holes_elastic(n=64, p=4, count=4, steps=10)
+    s = gpu_solver(w, precision="exact")
+    v, ms = s.autotune(reps=5)
+    assert v in (0, 1) and ms[0] > 0 and ms[1] > 0
+    assert ms[v] == min(ms)
+    assert s.info().tile_variant == v
+    s.close()
