@@ -221,7 +221,8 @@ def aggregate_replicas(step_ms, n_dof, world, device=None):
 # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, cold cache)
 # of the current kernel code on the benchmark workload; to be re-taken whenever the kernel
 # changes
-MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.368128e6 + 2.093312e6}
+MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.368128e6 + 2.093312e6,
+                    ("op_tc_exact_fused_cdm", "porous_voxel_64^3_p3", 1): 328.21e6 + 37.94e6}
 
 # arithmetic of each variant's element operator (the state and the update are FP64 in all)
 DTYPES = {"fp64": "f64",
