@@ -69,7 +69,7 @@ enum { IBFEM_CDM = 0, IBFEM_IMEX = 1, IBFEM_CDM_CONSISTENT = 2 };
 enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores                      */
        IBFEM_EXACT_TC = 1,      /* tcgen05 kind::f16, balanced 8-bit digit slices of u and
                                    K_ref (BF16) accumulated exactly per level (10 MMA chains),
-                                   level 0 assembled in FP64: about 32 significant bits      */
+                                   level 0 summed error-free: about 32 significant bits      */
        IBFEM_BF16X3_TC = 2,     /* tcgen05 kind::f16, BF16 hi/lo splits, 3 passes, FP32 acc. */
        IBFEM_BF16_TC = 3        /* tcgen05 kind::f16, one BF16 pass, FP32 accumulation      */ };
 enum { IBFEM_SRC_NONE = 0,

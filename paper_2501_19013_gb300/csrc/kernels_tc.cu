@@ -1,30 +1,35 @@
 // Tensor-core element operator fused with the FP64 central-difference update
 // (Eq. cdm of Buerchner et al., arXiv 2501.19013), for sm_103a (tcgen05 + TMEM).
 //
-// One CTA per tile of cells; it owns the lattice nodes of its tile and recomputes the
-// one-cell halo, so each node's sum over its cells is formed once, in a fixed order,
-// without atomics.  The uncut cells of the tile (one row of the MMA per halo'd cell,
-// M = 128) are contracted with the shared reference matrix K_ref on the tensor cores:
+// A persistent kernel: each CTA takes tiles of cells from a global counter (the host gives
+// the processing order, costliest first); it owns the lattice nodes of its tile and
+// recomputes the one-cell halo, so each node's sum over its cells is formed once, in a
+// fixed order, without atomics.  The cells of the halo'd tile (one row of the MMA per
+// cell, M = 128) are contracted with the shared reference matrix K_ref on the tensor
+// cores:
 //
 //   exact scheme (IBFEM_EXACT_TC) -- an exact-slice (Ozaki-type) product:
-//     x_mj = 2^(E_m - 31) sum_s d_s 2^(24 - 8 s),  K_ij = 2^(F_i - 31) sum_t c_t 2^(24 - 8 t)
-//     with balanced 8-bit digits d_s, c_t (|digit| <= 256, exact in BF16), E_m the row's
-//     largest exponent and F_i the K row's.  Products of digits accumulate EXACTLY in the
-//     FP32 accumulators of tcgen05.mma kind::f16 (integers below 2^24), one TMEM accumulator
-//     per level l = s + t <= 3 (10 MMA chains).  Level 0 goes to FP64 exactly; levels 1-3
-//     are combined in FP32 (they are 2^-8 smaller).  The node sums of level 0 are formed in
-//     FP64, so the cancellation in K u (element products ~ lambda_max |u|, the sum much
-//     smaller) costs no precision; the result carries about 32 significant bits.
+//     x_j = 2^(E - 1054) sum_s d_s 2^(24 - 8 s),  K_ij = 2^(F_i - 31) sum_t c_t 2^(24 - 8 t)
+//     with balanced 8-bit digits d_s, c_t (|digit| <= 256, exact in BF16), E the largest
+//     biased FP64 exponent of the tile's node patch and F_i the K row's.  Products of
+//     digits accumulate EXACTLY in the FP32 accumulators of tcgen05.mma kind::f16 (integers
+//     below 2^24), one TMEM accumulator per level l = s + t <= 3 (10 MMA chains).  The drain
+//     scales level 0 and the combined levels 1-3 by a power of two (exact); the node sums of
+//     level 0 are error-free FP32 sums, so the cancellation in K u (element products
+//     ~ lambda_max |u|, the sum much smaller) costs no precision before the one rounding of
+//     the residual to FP32; the result carries about 32 significant bits.
 //   bf16x3 / bf16 -- hi/lo BF16 splits with three MMA passes (hi.hi + hi.lo + lo.hi), or one
 //     pass, accumulated in FP32 (the plain mixed-precision contraction).
 //
 // Cut cells replace their rows with K^e x_e computed on the CUDA cores in double-FP32
-// arithmetic (two-slice FP32 matrices, error-free products and sums).  Per owned DOF:
-// (K u)_i = hi (FP64) + lo (FP32), r = F_i - K u (FP32 after the FP64 cancellation),
-// delta = (dt^2/m_i) r with a two-slice FP32 dt^2/m, widened to FP64 by bit manipulation,
-// and u^{k+1} = (2 u^k - u^{k-1}) + delta in FP64: two FP64 operations per DOF plus one per
-// extra cell sharing the node, the only FP64 arithmetic of the step.
-// The K_ref digit image is copied into shared memory with the bulk-async (TMA) engine.
+// arithmetic (FP32 (hi, lo) matrix pairs, error-free products and sums).  Per owned DOF:
+// r = -(K u)_i rounded once to FP32, delta = (dt^2/m_i) r with a two-slice FP32 dt^2/m,
+// widened to FP64 by bit manipulation, and u^{k+1} = (2 u^k - u^{k-1}) + delta in FP64: two
+// FP64 operations per DOF, the only FP64 arithmetic of the step besides the loads, which
+// are added per tile in FP64 (u^{k+1} += dt^2/m F_k).
+// The FP64 node patch of the next tile is loaded with cp.async while the current one is
+// finished; the K_ref digit image is copied into shared memory with the bulk-async (TMA)
+// engine once per CTA (per member image in the batched form).
 #include <algorithm>
 #include <cstdint>
 

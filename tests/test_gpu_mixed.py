@@ -2,7 +2,7 @@
 
 Schemes of the element contraction on the tensor cores:
   exact  -- balanced 8-bit digit slices of u and K_ref in BF16, ten MMA chains accumulated
-            exactly per level, level 0 assembled in FP64 (about 32 significant bits);
+            exactly per level, level 0 summed error-free (about 32 significant bits);
   bf16x3 -- BF16 hi/lo splits, three passes, FP32 accumulation;
   bf16   -- one BF16 pass, FP32 accumulation.
 The state and the central-difference update stay FP64.  A mixed variant counts for the
