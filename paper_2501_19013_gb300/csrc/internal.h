@@ -83,6 +83,7 @@ struct ImexDev {
   double* Y;                 // n_cells * n_loc products K^e x_e
   int n_comp;                // connected components = CTAs of the solve
   const int32_t* comp_ptr;   // permuted-row ranges of the components
+  int max_comp;              // rows of the largest component (its vector in shared memory)
   const int64_t* g_ptr;      // residual gather per permuted row
   const int32_t* g_idx;
   const double* Fc;          // spatial load on the c-DOFs (permuted rows), or null
@@ -94,6 +95,7 @@ struct ImexDev {
   const double* dinv;        // 1 / L_rr
   const int32_t *f_lvl, *f_rows, *comp_flvl;
   const int32_t *b_lvl, *b_rows, *comp_blvl;
+  const int4 *f_sched, *b_sched;   // per level and warp: {row, first entry, end, rows in the level}
   const int64_t* perm;       // permuted row -> c index
   const int64_t* c_dof;      // c index -> lattice DOF
   double* vc;

@@ -130,6 +130,8 @@ void Handle::build_device() {
     D.Y = static_cast<double*>(dalloc(std::max<size_t>(I.ccells.size(), 1) * s.n_loc * sizeof(double)));
     D.n_comp = (int)I.comp_ptr.size() - 1;
     D.comp_ptr = upload(I.comp_ptr);
+    D.max_comp = 0;
+    for (int c = 0; c < D.n_comp; ++c) D.max_comp = std::max(D.max_comp, I.comp_ptr[c + 1] - I.comp_ptr[c]);
     D.g_ptr = upload(I.g_ptr);
     D.g_idx = upload(I.g_idx);
     D.work = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
@@ -377,6 +379,30 @@ void Handle::imex_upload_factor() {
   }
   std::vector<double> dinv(I.n_c);
   for (int64_t r = 0; r < I.n_c; ++r) dinv[r] = 1.0 / L.Ux[L.Up[r]];
+  // per level and warp (32 per CTA): the warp's first row of the level with its entry range
+  // (forward: L rows without the trailing diagonal; backward: L^T rows without the leading one)
+  auto sched = [&](const std::vector<int32_t>& lp, const std::vector<int32_t>& lr, bool fwd) {
+    const size_t nl = lp.size() - 1;
+    std::vector<int32_t> v(nl * 32 * 4, 0);
+    for (size_t lv = 0; lv < nl; ++lv)
+      for (int wq = 0; wq < 32; ++wq) {
+        int32_t* e = &v[(lv * 32 + wq) * 4];
+        const int q = lp[lv] + wq;
+        e[3] = lp[lv + 1] - lp[lv];
+        if (q >= lp[lv + 1]) {
+          e[0] = -1;
+          continue;
+        }
+        const int r = lr[q];
+        e[0] = r;
+        e[1] = (int32_t)(fwd ? L.Lp[r] : L.Up[r] + 1);
+        e[2] = (int32_t)(fwd ? L.Lp[r + 1] - 1 : L.Up[r + 1]);
+      }
+    return v;
+  };
+  if (nnz > (size_t)INT32_MAX) throw std::runtime_error("IMEX factor too large for 32-bit schedule entries");
+  D.f_sched = reinterpret_cast<const int4*>(upload(sched(L.fwd_level_ptr, L.fwd_rows, true)));
+  D.b_sched = reinterpret_cast<const int4*>(upload(sched(L.bwd_level_ptr, L.bwd_rows, false)));
   auto cp = [&](const void* dst, const void* src, size_t bytes) {
     check(cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, stream), "factor upload");
   };
