@@ -16,7 +16,7 @@ Three geometry descriptions are supported:
 * rotated box: the physical domain is a cube of edge ``l_p`` rotated about the centre of
   the extended cube (the paper's benchmark, Sec. 3.1).
 
-Readings of the paper (listed in DESIGN.md): tangency (distance == r) counts as not cut;
+Readings of the paper where it is silent: tangency (distance == r) counts as not cut;
 a box covered by the union of two holes but by neither alone is classified CUT (its
 quadrature then resolves alpha pointwise).
 

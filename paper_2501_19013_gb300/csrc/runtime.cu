@@ -619,7 +619,7 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
   in.need_consistent_mass = o.scheme != IBFEM_CDM;
   if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
       o.precision != IBFEM_BF16_TC)
-    throw std::invalid_argument("precision not supported by this build");
+    throw std::invalid_argument("unknown precision");
   if (!(o.rho > 0)) throw std::invalid_argument("rho must be > 0");
   if (stab) {
     in.stab = stab->kind;

@@ -8,7 +8,7 @@ from paper_2501_19013_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# FP64 parity bound of the spec contract: relative L2 <= 1e-10 after the configured steps
+# FP64 parity bound: relative L2 <= 1e-10 against the oracle after the configured steps
 TOL = 1e-10
 
 
