@@ -211,7 +211,9 @@ int ibfem_step_timed(ibfem_t* h, int64_t n, void* flush_buf, size_t flush_bytes,
 /* Name of kernel slot `slot` of ibfem_step_timed ("" if out of range). */
 const char* ibfem_kernel_name(const ibfem_t* h, int slot);
 
-/* Synchronise the stream and report a non-finite state as IBFEM_ERR_DIVERGED. */
+/* Synchronise the stream; report a tensor-core kernel whose bounded wait (an mbarrier of
+ * the MMA or of the K_ref copy) gave up as IBFEM_ERR_TIMEOUT, and a non-finite state as
+ * IBFEM_ERR_DIVERGED.  The flags stay set (the state is no longer trustworthy). */
 int ibfem_sync(ibfem_t* h);
 
 /* Observer series recorded since set_observers/set_initial, oldest first: up to

@@ -1033,6 +1033,7 @@ int ibfem_sync(ibfem_t* h) {
   check(cudaStreamSynchronize(h->stream), "sync");
   int flags = 0;
   check(cudaMemcpy(&flags, h->dev.flags, sizeof(int), cudaMemcpyDeviceToHost), "flags");
+  if (flags & 2) return fail(IBFEM_ERR_TIMEOUT, "a bounded tensor-core wait gave up (results of that step are invalid)");
   if (flags & 1) return fail(IBFEM_ERR_DIVERGED, "non-finite value in the state");
   return IBFEM_OK;
   IBFEM_CATCH
@@ -1065,6 +1066,7 @@ int ibfem_sample(ibfem_t* h, int64_t max_rows, double* out, int64_t* rows) {
   *rows = r;
   int flags = 0;
   check(cudaMemcpy(&flags, h->dev.flags, sizeof(int), cudaMemcpyDeviceToHost), "flags");
+  if (flags & 2) return fail(IBFEM_ERR_TIMEOUT, "a bounded tensor-core wait gave up (results of that step are invalid)");
   if (flags & 1) return fail(IBFEM_ERR_DIVERGED, "non-finite value in the state");
   return IBFEM_OK;
   IBFEM_CATCH
