@@ -88,3 +88,21 @@ def test_voxel_blocks_share_cut_matrices():
     h = ib.from_workload(W.plate_one_hole(), host_only=True)
     assert h.info().n_cut_matrices == h.info().n_cut   # curved boundaries: no sharing
     h.close()
+
+
+def test_rotated_cube_workload_geometry():
+    """The benchmark's load centre lies on the cube face x' = -l/2 (Sec. 3.1), and every
+    observer lies in a kept cell (the oracle's classification)."""
+    from oracle.geometry import RotatedBox
+    w = W.rotated_cube(ne=6, p=2)
+    rb = w.rotated_box
+    T = rb[4:13].reshape(3, 3)
+    c = rb[1:4]
+    xl = np.asarray(w.source["x"])
+    loc = T.T @ (xl - c)
+    assert abs(loc[0] + rb[0] / 2) < 1e-12 and abs(loc[1]) < 1e-12 and abs(loc[2]) < 1e-12
+    d = OD.from_workload(w, assemble=False)
+    for x in w.observers:
+        d.locate(x)        # raises if the point is in no kept cell
+    box = RotatedBox(rb[0], c, T)
+    assert box.in_physical(w.observers).all()
