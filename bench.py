@@ -180,6 +180,49 @@ def run_serving(args):
     return out
 
 
+def run_multi_source(args, w, r):
+    """Several loads on the benchmark geometry: ``args.sources`` clones of the exact solver
+    (shared device geometry and matrices, own state and load), each with an edge traction
+    on another window of the left edge, advanced together by the batched exact kernel."""
+    from paper_2501_19013_gb300 import ibfem as ib
+    S = args.sources
+    src = r["solver"]
+    clones = [src.clone() for _ in range(S)]
+    for k, c in enumerate(clones):
+        y0 = 0.05 + 0.7 * k / max(S - 1, 1)
+        c.set_source("edge_traction", [y0, y0 + 0.2, 1.0, 0.0], w.f0)
+        c.set_initial()
+    warm = 64
+    n = -(-args.steps // 32) * 32
+    b = ib.Batch()
+    for c in clones:
+        b.add(c, warm + n)
+    b.run(warm)
+    b.sync()
+    t0 = time.perf_counter()
+    b.run(n)
+    b.sync()
+    el = time.perf_counter() - t0
+    done = b.poll()
+    failed = b.status()[1]
+    b.close()
+    inf_s, inf_c = src.info(), clones[0].info()
+    n_dof = inf_s.n_dof
+    out = {"sources": S, "steps": n, "completed": len(done), "failed": failed,
+           "dof_steps_per_s": S * n_dof * n / el, "ms_per_batched_step": el * 1e3 / n,
+           "single_problem_dof_steps_per_s": n_dof / (r["step_ms"] * 1e-3),
+           "device_bytes_fresh_handle": int(inf_s.device_bytes),
+           "shared_device_bytes": int(inf_s.shared_device_bytes),
+           "device_bytes_per_clone": int(inf_c.device_bytes - inf_c.shared_device_bytes),
+           "precision": "exact", "tile_variant": int(inf_c.tile_variant),
+           "loads": "edge traction x-direction on x = 0, y in [y0, y0 + 0.2], y0 = 0.05 ... 0.75",
+           "timing": "wall clock of ibfem_batch_run + ibfem_batch_sync after 64 warm-up steps; "
+                     "the members' states (2 x 8 B x n_dof each) exceed L2"}
+    for c in clones:
+        c.close()
+    return out
+
+
 def parse_variant(v, w):
     """'fp64' | 'exact' | 'bf16x3' | 'bf16' -> CDM with the workload's stabilisation;
     'imex' -> Newmark IMEX (FP64); 'cons' -> CDM with the consistent cut mass (FP64);
@@ -394,6 +437,8 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": rb["clocks"], "variants": variants_out}
+    if rank == 0 and world == 1 and args.sources > 0 and "exact" in results:
+        line["multi_source"] = run_multi_source(args, w, results["exact"])
     for r in results.values():
         r["solver"].close()
     if rank == 0 and world == 1 and args.serve_requests > 0:
@@ -415,6 +460,8 @@ def main():
     ap.add_argument("--dt", type=float, default=0.0, help="fixed dt instead of 0.9 dt_crit (profiling)")
     ap.add_argument("--run-steps", type=int, default=-1, help="steps of the accuracy run (-1: the workload's)")
     ap.add_argument("--run-time", type=float, default=0.0, help="simulated time of the accuracy run (overrides steps)")
+    ap.add_argument("--sources", type=int, default=8,
+                    help="loads of the shared-geometry multi-source run (0: none)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving run (0: none)")
     ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrival rate of the serving run (1/s)")
     ap.add_argument("--serve-slots", type=int, default=32, help="maximum concurrent members of the batch")

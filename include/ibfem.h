@@ -140,6 +140,9 @@ typedef struct {
                                  cells with equal voxel blocks share one set             */
     int32_t tile_variant;     /* tensor-core tile shape in use (0 full, 1 small)       */
     int32_t tile[3];          /* cells per tile and axis of the tensor-core kernel     */
+    size_t shared_device_bytes; /* part of device_bytes held jointly with the handle's
+                                 clones (or its source): geometry, cut-cell and
+                                 reference matrices; freed with the last of them          */
 } ibfem_info_t;
 
 /* ---- lifetime -------------------------------------------------------------------- */
@@ -153,7 +156,21 @@ typedef struct {
 int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry,
                  double alpha, const ibfem_stab* stab, const ibfem_options* opt,
                  ibfem_t** out);
-/* Free every resource of the handle (NULL is accepted). */
+/* Several loads on one discretisation (shared-geometry multi-source runs).  *out
+ * receives a new handle on the same grid, geometry, material, scheme, precision and
+ * tile shape as `src`, whose device geometry, cut-cell matrices, reference stiffness
+ * and tensor-core K_ref image it shares instead of holding a copy; it owns its state,
+ * load, observers, counters and dt^2 / M_L.  The clone starts at rest with no load and
+ * no observers, with src's dt if src has one (set_dt on either changes only that
+ * handle).  Each handle keeps the shared arrays alive: `src` may be destroyed first.
+ * A clone steps alone or as a member of a batch like any handle, and gives the results
+ * of a handle created from scratch on the same inputs, bit for bit.  `src` may be a
+ * batch member (nothing of its state is read).
+ * Errors: ARG (null argument; src solves a c-set, i.e. IMEX or the consistent-mass CDM
+ * with cut cells), STATE (src is host_only), OOM, CUDA.                               */
+int ibfem_clone(ibfem_t* src, ibfem_t** out);
+/* Free every resource of the handle (NULL is accepted).  Arrays shared with clones
+ * are freed with the last handle that uses them. */
 int ibfem_destroy(ibfem_t* h);
 /* Message of the last failed call on this thread ("" if none).  Valid until the next
  * failing call on the same thread. */

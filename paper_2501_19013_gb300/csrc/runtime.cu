@@ -52,8 +52,13 @@ void* Handle::dalloc(size_t bytes) {
       throw std::bad_alloc();
     }
   }
-  allocs.push_back(p);
-  device_bytes += bytes;
+  if (to_shared) {
+    shared->ptrs.push_back(p);
+    shared->bytes += bytes;
+  } else {
+    allocs.push_back(p);
+    device_bytes += bytes;
+  }
   return p;
 }
 
@@ -64,6 +69,16 @@ void Handle::dfree_all() {
   }
   allocs.clear();
   device_bytes = 0;
+  shared.reset();   // the last handle of a discretisation frees its shared arrays
+  to_shared = false;
+}
+
+DeviceShared::~DeviceShared() {
+  cudaSetDevice(device);
+  for (void* p : ptrs) {
+    if (dev_free) dev_free(p, alloc_ctx);
+    else cudaFree(p);
+  }
 }
 
 template <typename T>
@@ -101,6 +116,11 @@ void Handle::build_device() {
     pb.lat[k] = (int)s.lat[k];
   }
   pb.n_lat_dof = s.n_lat_dof;
+  shared = std::make_shared<DeviceShared>();
+  shared->device = opt.device;
+  shared->dev_free = opt.dev_free;
+  shared->alloc_ctx = opt.alloc_ctx;
+  to_shared = true;   // geometry and matrices: shared with clones
   pb.cls = upload(s.cls);
   pb.cut_index = upload(s.cut_index);
   pb.cut_mat = upload(s.cut_mat);
@@ -108,6 +128,7 @@ void Handle::build_device() {
   pb.n_cut = (int)s.n_cut;
   pb.Kref = upload(s.Kref);
   pb.Kcut = upload(s.Kcut);
+  to_shared = false;
   pb.Ycut = static_cast<double*>(dalloc(std::max<int64_t>(s.n_cut, 1) * s.n_loc * sizeof(double)));
   // 1/M_L (dt = 1 until set_dt) and 1/sqrt(M_L)
   std::vector<double> minv(s.n_lat_dof, 0.0), sinv(s.n_lat_dof, 0.0);
@@ -120,7 +141,9 @@ void Handle::build_device() {
     for (int64_t ci = 0; ci < imex_host.n_c; ++ci) sinv[imex_host.c_dof[ci]] = 0.0;  // d-block only
   d_minv = upload(minv);
   pb.minv = d_minv;
+  to_shared = !imex;   // IMEX zeroes its c-DOFs in 1/sqrt(M_L): then it is the handle's own
   pb.sinv = upload(sinv);
+  to_shared = false;
   if (imex) {
     const ImexData& I = imex_host;
     ImexDev& D = imex_dev;
@@ -208,6 +231,7 @@ void Handle::build_device() {
         }
       }
     }
+    to_shared = true;
     pb.tc_bimg = upload(img);
     pb.tc_frow = upload(frow);
     tc_img_host = img;
@@ -223,6 +247,7 @@ void Handle::build_device() {
         k32[2 * (c * nl2 + q) + 1] = (float)(v - (double)h);
       }
     pb.Kcut32 = upload(k32);
+    to_shared = false;
     std::vector<float> m32(2 * (size_t)s.n_lat_dof, 0.f);
     for (int64_t i = 0; i < s.n_lat_dof; ++i)
       if (s.ML[i] > 0) {
@@ -239,6 +264,57 @@ void Handle::build_device() {
   lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
   scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
   check(cudaStreamSynchronize(stream), "setup sync");
+}
+
+// a clone: the source's shared arrays, its own state, work arrays, counters and
+// dt^2 / M_L (copied from the source, so the source's dt carries over); no load and no
+// observers until they are set
+void Handle::build_clone(const Handle& src) {
+  const Setup& s = setup;
+  DevProblem& pb = dev;
+  pb = src.dev;
+  pb.src_ptr = nullptr;
+  pb.src_dof = nullptr;
+  pb.src_val = nullptr;
+  pb.f_e = 0.0;
+  pb.tsrc_ptr = nullptr;
+  pb.tsrc_dof = nullptr;
+  pb.tsrc_val = nullptr;
+  pb.n_obs_rows = 0;
+  pb.obs_dof = nullptr;
+  pb.obs_w = nullptr;
+  pb.ring = nullptr;
+  pb.ring_cap = 0;
+  pb.imex_vc = nullptr;
+  pb.imex_ac = nullptr;
+  pb.Ycut = static_cast<double*>(dalloc(std::max<int64_t>(s.n_cut, 1) * s.n_loc * sizeof(double)));
+  d_minv = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+  check(cudaMemcpyAsync(d_minv, src.d_minv, s.n_lat_dof * sizeof(double), cudaMemcpyDeviceToDevice, stream), "minv");
+  pb.minv = d_minv;
+  for (int b = 0; b < 2; ++b) {
+    U[b] = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+    check(cudaMemsetAsync(U[b], 0, s.n_lat_dof * sizeof(double), stream), "memset");
+  }
+  W = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+  check(cudaMemsetAsync(W, 0, s.n_lat_dof * sizeof(double), stream), "memset");
+  counters = static_cast<unsigned long long*>(dalloc(4 * sizeof(unsigned long long)));
+  check(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), stream), "memset");
+  pb.step = counters;
+  pb.done = reinterpret_cast<unsigned int*>(counters + 1);
+  pb.flags = reinterpret_cast<int*>(counters + 2);
+  pb.tile_counter = reinterpret_cast<int*>(counters + 3);
+  partials = static_cast<double*>(dalloc(2 * (size_t)n_blocks * sizeof(double)));
+  if (src.d_minv32) {
+    d_minv32 = static_cast<float*>(dalloc(2 * s.n_lat_dof * sizeof(float)));
+    check(cudaMemcpyAsync(d_minv32, src.d_minv32, 2 * s.n_lat_dof * sizeof(float), cudaMemcpyDeviceToDevice,
+                          stream), "minv32");
+    pb.minv32 = d_minv32;
+    build_tc_tiles();   // the source's tile order may be its own array (a later tile variant)
+  }
+  scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
+  lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
+  scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
+  check(cudaStreamSynchronize(stream), "clone sync");
 }
 
 // tile grid of the tensor-core kernel for the current tile variant and the processing
@@ -688,6 +764,44 @@ int ibfem_upload(ibfem_t* h) {
   IBFEM_CATCH
 }
 
+int ibfem_clone(ibfem_t* src, ibfem_t** out) {
+  if (!src || !out) return fail(IBFEM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (src->opt.host_only) return fail(IBFEM_ERR_STATE, "handle was created host_only");
+  if (src->imex) return fail(IBFEM_ERR_ARG, "clones are for the lumped-mass CDM (this handle solves a c-set)");
+  IBFEM_TRY
+  check(cudaSetDevice(src->opt.device), "cudaSetDevice");
+  std::unique_ptr<ibfem_t> h(new ibfem_t(src->setup_p));
+  h->opt = src->opt;
+  h->input = src->input;
+  h->consistent = src->consistent;
+  h->beta = src->beta;
+  h->tc_variant = src->tc_variant;
+  for (int k = 0; k < 3; ++k) h->tile[k] = src->tile[k];
+  h->n_blocks = src->n_blocks;
+  h->tc_img_host = src->tc_img_host;
+  h->tc_frow_host = src->tc_frow_host;
+  h->shared = src->shared;
+  h->dt = src->dt;
+  h->have_dt = src->have_dt;
+  h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  if (!h->stream) {
+    check(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    h->own_stream = true;
+  }
+  try {
+    h->build_clone(*src);
+  } catch (...) {
+    cudaStreamSynchronize(h->stream);
+    h->dfree_all();
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    throw;
+  }
+  *out = h.release();
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
 int ibfem_destroy(ibfem_t* h) {
   if (!h) return IBFEM_OK;
   if (h->batch) batch_forget(h);   // drains the batch stream, then drops the member
@@ -725,7 +839,8 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
     out->nnz_L = (int64_t)h->imex_host.chol.Lx.size();
     out->n_levels = (int32_t)h->imex_host.chol.fwd_level_ptr.size() - 1;
   }
-  out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes;
+  out->shared_device_bytes = h->shared ? h->shared->bytes : 0;
+  out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes + out->shared_device_bytes;
   out->n_cut_matrices = s.n_cut_mat;
   out->tile_variant = h->tc_variant;
   for (int k = 0; k < 3; ++k) out->tile[k] = h->tc_tile[k];

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <vector>
 
 #include "../../include/ibfem.h"
@@ -14,10 +15,27 @@ namespace ibfem {
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: parity preserved)
 constexpr int kPowerChunk = 32;   // power iterations between host convergence checks
 
+// Device arrays of one discretisation that its clones share: cell classes, cut-cell
+// indices and matrices (FP64 and FP32 pairs), K_ref and its tensor-core image, and
+// 1/sqrt(M_L).  Freed when the last handle using them is destroyed.
+struct DeviceShared {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  int device = 0;
+  void (*dev_free)(void*, void*) = nullptr;
+  void* alloc_ctx = nullptr;
+  ~DeviceShared();
+};
+
 struct Handle {
+  Handle() = default;
+  explicit Handle(std::shared_ptr<Setup> s) : setup_p(std::move(s)) {}
   ibfem_options opt{};
   SetupInput input;
-  Setup setup;
+  std::shared_ptr<Setup> setup_p = std::make_shared<Setup>();   // host discretisation (shared by clones)
+  Setup& setup = *setup_p;
+  std::shared_ptr<DeviceShared> shared;   // device arrays shared with clones
+  bool to_shared = false;                 // dalloc places new arrays in `shared`
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   DevProblem dev{};
@@ -73,6 +91,7 @@ struct Handle {
   void to_lattice(const double* kept, std::vector<double>& lat) const;
   void from_lattice(const std::vector<double>& lat, double* kept) const;
   void build_device();
+  void build_clone(const Handle& src);
   void invalidate_graphs();
   // optional per-kernel timing: when `timing` is set, enqueue_step records an event
   // pair around every launch and accumulates into slot_ms after a synchronise
@@ -96,4 +115,6 @@ void batch_forget(Handle* h);
 
 }  // namespace ibfem
 
-struct ibfem_s : ibfem::Handle {};
+struct ibfem_s : ibfem::Handle {
+  using Handle::Handle;
+};

@@ -64,7 +64,8 @@ class Info(C.Structure):
                 ("n_loc", C.c_int32), ("ncomp", C.c_int32), ("precision", C.c_int32),
                 ("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double),
                 ("lambda_ref", C.c_double), ("device_bytes", C.c_size_t),
-                ("n_cut_matrices", C.c_int64), ("tile_variant", C.c_int32), ("tile", C.c_int32 * 3)]
+                ("n_cut_matrices", C.c_int64), ("tile_variant", C.c_int32), ("tile", C.c_int32 * 3),
+                ("shared_device_bytes", C.c_size_t)]
 
 
 _lib = None
@@ -105,6 +106,7 @@ def lib():
         "ibfem_apply_operator_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
         "ibfem_upload": (C.c_int, [vp]),
+        "ibfem_clone": (C.c_int, [vp, C.POINTER(vp)]),
         "ibfem_set_tile_variant": (C.c_int, [vp, C.c_int]),
         "ibfem_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), DP]),
         "ibfem_batch_create": (C.c_int, [vp, C.c_int, C.POINTER(vp)]),
@@ -228,6 +230,20 @@ class Solver:
     def upload(self):
         """Move a host-only handle onto its device (``ibfem_upload``)."""
         _check(lib().ibfem_upload(self.h))
+
+    def clone(self):
+        """A new solver on this discretisation (``ibfem_clone``): shares the device geometry
+        and matrices, owns its state, load, observers and dt (initially this one's)."""
+        h = C.c_void_p()
+        _check(lib().ibfem_clone(self.h, C.byref(h)))
+        c = Solver.__new__(Solver)
+        c.h = h
+        c.dim, c.n_dof, c.ncomp, c.n_loc = self.dim, self.n_dof, self.ncomp, self.n_loc
+        c._keep = []
+        for k in ("_alloc_cb", "_free_cb"):   # the clone may free shared arrays through them
+            if hasattr(self, k):
+                setattr(c, k, getattr(self, k))
+        return c
 
     def set_tile_variant(self, variant):
         _check(lib().ibfem_set_tile_variant(self.h, int(variant)))

@@ -106,3 +106,17 @@ def test_rotated_cube_workload_geometry():
         d.locate(x)        # raises if the point is in no kept cell
     box = RotatedBox(rb[0], c, T)
     assert box.in_physical(w.observers).all()
+
+
+def test_clone_needs_a_device_handle():
+    """ibfem_clone shares device arrays, so it refuses a host-only source (STATE) and a
+    null source (ARG) before touching the device."""
+    import ctypes as C
+    h = ib.from_workload(W.plate_one_hole(), host_only=True)
+    with pytest.raises(ib.IbfemError) as ei:
+        h.clone()
+    assert ei.value.code == ib.ERR_STATE
+    out = C.c_void_p()
+    assert ib.lib().ibfem_clone(None, C.byref(out)) == ib.ERR_ARG
+    assert h.info().shared_device_bytes == 0
+    h.close()
