@@ -651,6 +651,15 @@ void attach_device(ibfem_t* h) {
   h->build_device();
   if (h->consistent && h->imex) h->prepare_consistent();
 }
+
+// undo a failed attach_device or build_clone: free what was allocated and the private stream
+void detach_device(ibfem_t* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->dfree_all();
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  h->stream = nullptr;
+  h->own_stream = false;
+}
 }  // namespace
 
 extern "C" {
@@ -736,7 +745,14 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
     h->consistent = o.scheme == IBFEM_CDM_CONSISTENT;
     h->beta = h->consistent ? 0.0 : 0.25;
   }
-  if (!o.host_only) attach_device(h.get());
+  if (!o.host_only) {
+    try {
+      attach_device(h.get());
+    } catch (...) {
+      detach_device(h.get());
+      throw;
+    }
+  }
   *out = h.release();
   return IBFEM_OK;
   IBFEM_CATCH
@@ -751,12 +767,7 @@ int ibfem_upload(ibfem_t* h) {
   try {
     attach_device(h);
   } catch (...) {
-    // back to a host-only handle: release what was allocated
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    h->dfree_all();
-    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
-    h->stream = nullptr;
-    h->own_stream = false;
+    detach_device(h);   // back to a host-only handle
     h->opt.host_only = 1;
     throw;
   }
@@ -792,9 +803,7 @@ int ibfem_clone(ibfem_t* src, ibfem_t** out) {
   try {
     h->build_clone(*src);
   } catch (...) {
-    cudaStreamSynchronize(h->stream);
-    h->dfree_all();
-    if (h->own_stream) cudaStreamDestroy(h->stream);
+    detach_device(h.get());
     throw;
   }
   *out = h.release();
