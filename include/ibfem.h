@@ -255,6 +255,13 @@ int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells);
 /* Element stiffness (n_loc x n_loc, row-major) used for cell `cell` (shared reference
  * matrix for uncut cells); optional lumped diagonal (n_loc). Errors: ARG (outside).   */
 int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml);
+/* Consistent element mass (n_loc x n_loc, row-major) of cell `cell` as the consistent-mass
+ * schemes use it: for a cut cell the alpha-integrated space-tree mass M^o (Sec. 2.2), plus
+ * eps M^s under eigenvalue stabilisation (Eq. epsilon_stabilization); for an uncut cell
+ * the GLL-quadrature mass, which is diagonal (Sec. 2.4).  Host data only (valid for
+ * host_only handles).  Errors: ARG (null M, cell outside or out of range), STATE (a cut
+ * cell of a handle with scheme IBFEM_CDM, which keeps only the lumped cut masses).       */
+int ibfem_get_element_mass(ibfem_t* h, int64_t cell, double* M);
 
 /* ---- tile shape -------------------------------------------------------------------- */
 

@@ -1421,4 +1421,20 @@ int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml) {
   return IBFEM_OK;
 }
 
+int ibfem_get_element_mass(ibfem_t* h, int64_t cell, double* M) {
+  if (!h || !M) return fail(IBFEM_ERR_ARG, "null argument");
+  const Setup& s = h->setup;
+  if (cell < 0 || cell >= s.n_elem || s.cls[cell] == kOutside) return fail(IBFEM_ERR_ARG, "cell is outside or out of range");
+  const int nl = s.n_loc;
+  if (s.cls[cell] == kCut) {
+    if (s.Mcut.empty()) return fail(IBFEM_ERR_STATE, "consistent cut masses are kept by the IMEX and consistent-mass schemes only");
+    const size_t ci = (size_t)s.cut_mat[s.cut_index[cell]];
+    std::copy(&s.Mcut[ci * nl * nl], &s.Mcut[(ci + 1) * nl * nl], M);
+  } else {
+    std::fill(M, M + (size_t)nl * nl, 0.0);
+    for (int i = 0; i < nl; ++i) M[(size_t)i * nl + i] = s.mref[i];
+  }
+  return IBFEM_OK;
+}
+
 }  // extern "C"

@@ -103,6 +103,7 @@ def lib():
         "ibfem_get_lumped_mass": (C.c_int, [vp, DP]),
         "ibfem_get_cut_cells": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "ibfem_get_element": (C.c_int, [vp, C.c_int64, DP, DP]),
+        "ibfem_get_element_mass": (C.c_int, [vp, C.c_int64, DP]),
         "ibfem_apply_operator_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
         "ibfem_upload": (C.c_int, [vp]),
@@ -337,6 +338,13 @@ class Solver:
         ml = np.zeros(self.n_loc)
         _check(lib().ibfem_get_element(self.h, int(cell), _dp(K), _dp(ml)))
         return K, ml
+
+
+    def element_mass(self, cell):
+        """Consistent element mass of the consistent-mass schemes (``ibfem_get_element_mass``)."""
+        M = np.zeros((self.n_loc, self.n_loc))
+        _check(lib().ibfem_get_element_mass(self.h, int(cell), _dp(M)))
+        return M
 
 
 class Batch:

@@ -120,3 +120,27 @@ def test_clone_needs_a_device_handle():
     assert ib.lib().ibfem_clone(None, C.byref(out)) == ib.ERR_ARG
     assert h.info().shared_device_bytes == 0
     h.close()
+
+
+def test_element_mass_of_the_consistent_schemes():
+    """ibfem_get_element_mass: the cut cells' consistent mass M^o + eps M^s (Eq.
+    epsilon_stabilization) as the oracle integrates and stabilises it, the GLL diagonal
+    for uncut cells; a lumped-mass CDM handle keeps no consistent cut mass (STATE)."""
+    w = W.plate_holes_imex(n=20, p=3, count=3, seed=2).with_(scheme="cdm_consistent", stab="evs",
+                                                              eps=1e-4, f_lambda=1e-2)
+    d = OD.from_workload(w)
+    s = ib.from_workload(w, host_only=True)
+    for e in d.cut:
+        M = s.element_mass(e)
+        Mo = d.M_cut_stab[e]
+        np.testing.assert_allclose(M, Mo, rtol=1e-10, atol=1e-10 * np.abs(Mo).max())
+        assert not np.allclose(M, d.M_cut_cons[e])      # the stabilisation is in
+    e = d.uncut[0]
+    np.testing.assert_allclose(s.element_mass(e), np.diag(d.m_gll), rtol=1e-14)
+    s.close()
+    h = ib.from_workload(w.with_(scheme="cdm"), host_only=True)
+    with pytest.raises(ib.IbfemError) as ei:
+        h.element_mass(d.cut[0])
+    assert ei.value.code == ib.ERR_STATE
+    np.testing.assert_allclose(h.element_mass(e), np.diag(d.m_gll), rtol=1e-14)
+    h.close()
