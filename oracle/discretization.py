@@ -141,8 +141,11 @@ class Discretization:
         lo0 = self.lo
         hi0 = self.lo + self.h
         X, W, A = full_cell_quadrature(lo0, hi0, self.p)
-        self.K_ref, self.M_full = self._matrices(lo0, hi0, X, W, A)
+        self.K_ref, _ = self._matrices(lo0, hi0, X, W, A)
         self.m_gll = el.gll_mass_diagonal(self.p, self.h, self.rho, self.ncomp)
+        # M^f of the eigenvalue stabilisation (Sec. 2.5): the mass of a cell lying wholly in
+        # Omega as the SCM forms it, with GLL quadrature (Sec. 2.4), hence diagonal
+        self.M_full = np.diag(self.m_gll)
         self.lam_ref = element_lambda_max(self.K_ref, self.m_gll)
 
     def _cut_matrices(self, e):

@@ -4,7 +4,11 @@
   with M^s built from the eigenvectors of M^o whose eigenvalues are below
   f_lambda * lambda_max, scaled so that its largest entry equals the largest entry of
   the full (uncut) element mass M^f.  M^o is the alpha-integrated consistent matrix
-  (reading: the paper combines EVS with alpha = 1e-12, Table 2 and Table 3).
+  (reading: the paper combines EVS with alpha = 1e-12, Table 2 and Table 3).  M^f is
+  read as the SCM's own mass of a cell inside Omega: GLL quadrature, a diagonal matrix
+  (Sec. 2.4); with it the critical time steps of the consistent-mass CDM with EVS in
+  Table 3 come out to five digits for p = 3, while the exactly integrated full mass
+  misses them by 3-8 %.
 * HRZ / diagonal-scaling lumping (Sec. 2.4): m~_ii = m^e m_ii / sum_j m_jj, where the
   element mass m^e is taken as the sum of all entries of the (stabilised) consistent
   matrix, which equals the integral of alpha^FCM rho by partition of unity.

@@ -766,13 +766,12 @@ Setup build_setup(const SetupInput& in) {
   ElementIntegrator integ(s, in);
   const int nl = s.n_loc;
   s.Kref.assign(nl * nl, 0.0);
-  std::vector<double> Mfull(nl * nl, 0.0);
   {
+    std::vector<double> Mgl(nl * nl, 0.0);   // GL mass of the full cell (not used by the SCM)
     double clo[3] = {s.lo[0], s.lo[1], s.lo[2]}, chi[3];
     for (int k = 0; k < 3; ++k) chi[k] = clo[k] + s.h[k];
-    integ.accumulate(geo, clo, clo, chi, 1.0, s.Kref.data(), Mfull.data());
+    integ.accumulate(geo, clo, clo, chi, 1.0, s.Kref.data(), Mgl.data());
     ElementIntegrator::symmetrize(nl, s.Kref.data());
-    ElementIntegrator::symmetrize(nl, Mfull.data());
   }
   s.mref.assign(nl, 0.0);
   for (int j = 0; j < s.nn_loc; ++j) {
@@ -792,7 +791,10 @@ Setup build_setup(const SetupInput& in) {
     return ev[nl - 1];
   };
   s.lambda_ref = lambda_max_lumped(s.Kref.data(), s.mref.data());
-  double mfull_max = *std::max_element(Mfull.begin(), Mfull.end());
+  // M^f of the eigenvalue stabilisation (Sec. 2.5): the mass of a cell inside the physical
+  // domain as the SCM integrates it, i.e. with GLL quadrature (diagonal); its largest entry
+  // scales M^s
+  double mfull_max = *std::max_element(s.mref.begin(), s.mref.end());
 
   // distinct cut cells: with a voxel image holding a whole number r_k of voxels per cell and
   // axis (prod r_k <= 64), a cut cell's integrals depend only on its voxel block, so cells
