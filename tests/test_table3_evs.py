@@ -1,13 +1,14 @@
 """The paper's critical time steps of the consistent-mass CDM with eigenvalue stabilisation
 (Sec. 2.5) on the rotated cube (golden values in tests/golden/timing_table_evs_dt_crit.txt),
-from the library's host setup on the CPU: its element stiffnesses and consistent element
-masses (M^o + eps M^s for cut cells, ``ibfem_get_element_mass``) are assembled, and the
-largest eigenvalue of M^{-1} K comes from ARPACK; dt_crit = 2 / sqrt(lambda_max) (Sec. 2.3).
+on the CPU, twice: from the oracle's discretisation (cut cells integrated in a process
+pool), and from the library's host setup (element stiffnesses and consistent element
+masses M^o + eps M^s through ``ibfem_get_element_mass``).  Each assembles K and the
+consistent mass M; the largest eigenvalue of M^{-1} K comes from ARPACK, and
+dt_crit = 2 / sqrt(lambda_max) (Sec. 2.3).
 
-This pins the reading of the scale of M^s: with M^f the GLL mass of a full cell the paper's
-values come out to five digits, with the exactly integrated full mass they miss by 3-8 %.
-The oracle's stabilisation is tied to the same numbers through the element-by-element
-comparison of the two setups (tests/test_host_setup.py)."""
+This pins the oracle's reading of the scale of M^s: with M^f the GLL mass of a full cell
+the paper's values come out to five digits, with the exactly integrated full mass they miss
+by 3-8 %."""
 import os
 
 import numpy as np
@@ -51,6 +52,23 @@ def assembled(s, d):
     return mk(rk, ck, vk), mk(rm, cm, vm)
 
 
+def dt_crit(K, M):
+    lu = spla.splu(M.tocsc())
+    op = spla.LinearOperator(K.shape, matvec=lambda x: lu.solve(K @ x))
+    lam = spla.eigs(op, k=1, which="LR", tol=1e-12, v0=np.ones(K.shape[0]), maxiter=50000)[0][0].real
+    return 2.0 / np.sqrt(lam)
+
+
+@pytest.mark.parametrize("p,ne,alpha,eps,dt_paper", rows())
+def test_oracle_evs_dt_crit_matches_the_paper(p, ne, alpha, eps, dt_paper):
+    from helpers import oracle_disc_parallel
+    w = W.rotated_cube(ne=ne, p=p, alpha=alpha, stab="evs", eps=eps, quad_depth=p + 1)
+    assert w.f_lambda == 1e-2
+    d = oracle_disc_parallel(w)
+    dt = dt_crit(d.K, d.consistent_mass(stabilised=True))
+    assert abs(dt - dt_paper) <= 2e-4 * dt_paper   # four significant digits
+
+
 @pytest.mark.parametrize("p,ne,alpha,eps,dt_paper", rows())
 def test_evs_dt_crit_matches_the_paper(p, ne, alpha, eps, dt_paper):
     w = W.rotated_cube(ne=ne, p=p, alpha=alpha, stab="evs", eps=eps, quad_depth=p + 1)
@@ -61,8 +79,5 @@ def test_evs_dt_crit_matches_the_paper(p, ne, alpha, eps, dt_paper):
     assert s.info().n_dof == d.n_dof
     K, M = assembled(s, d)
     s.close()
-    lu = spla.splu(M.tocsc())
-    op = spla.LinearOperator(K.shape, matvec=lambda x: lu.solve(K @ x))
-    lam = spla.eigs(op, k=1, which="LR", tol=1e-12, v0=np.ones(K.shape[0]), maxiter=50000)[0][0].real
-    dt = 2.0 / np.sqrt(lam)
+    dt = dt_crit(K, M)
     assert abs(dt - dt_paper) <= 2e-4 * dt_paper   # four significant digits
