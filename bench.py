@@ -438,7 +438,10 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": rb["clocks"], "variants": variants_out}
     if rank == 0 and world == 1 and args.sources > 0 and "exact" in results:
-        line["multi_source"] = run_multi_source(args, w, results["exact"])
+        try:
+            line["multi_source"] = run_multi_source(args, w, results["exact"])
+        except ib.IbfemError as e:          # reported in the line; the headline stands
+            line["multi_source"] = {"sources": args.sources, "error": str(e)}
     for r in results.values():
         r["solver"].close()
     if rank == 0 and world == 1 and args.serve_requests > 0:
