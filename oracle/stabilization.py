@@ -21,7 +21,8 @@ Pins: the stabilisation matrix is a symmetric idempotent projector times a scale
 eps M^s is PSD, HRZ preserves the element mass and positivity, and the mass-scaled
 global lambda_max respects the element bound (tests/test_oracle_stabilization.py); the
 critical time step of the consistent-mass CDM with EVS on the paper's rotated cube
-(p = 3, ne = 13, eps = 1e-6) equals the paper's to five digits (tests/test_table3_evs.py).
+(p = 3, ne = 13, eps = 1e-6) equals the paper's to five digits
+(tests/test_timing_table_cpu.py).
 """
 from __future__ import annotations
 

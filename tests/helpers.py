@@ -33,6 +33,35 @@ def oracle_disc_parallel(w, workers=None):
     return d
 
 
+def _oracle_cut_parts(args):
+    from oracle.quadrature import cut_cell_quadrature
+    d, cells = args
+    out = {}
+    for e in cells:
+        lo, hi = d.elem_box(e)
+        X, Wq, A = cut_cell_quadrature(d.geom, lo, hi, d.p, d.quad_depth, 0.0)
+        out[e] = d._matrices(lo, hi, X, Wq, A) + d._matrices(lo, hi, X, Wq, 1.0 - A)
+    return out
+
+
+def oracle_cut_parts(w, workers=None):
+    """The oracle's cut-cell integrals of ``w`` split by the indicator: per cut cell
+    (K_phys, M_phys, K_fict, M_fict), the physical and the fictitious part, so that the
+    matrices for any alpha are K_phys + alpha K_fict and M_phys + alpha M_fict (the
+    integrands are linear in alpha^FCM).  Computed by a pool of spawned processes with the
+    oracle's own quadrature and element routines; returns (discretisation without cut
+    matrices, parts)."""
+    import multiprocessing as mp
+    d = OD.from_workload(w, assemble=False)
+    n = max(1, min(workers or os.cpu_count() or 1, 8, len(d.cut)))
+    chunks = [list(d.cut)[i::n] for i in range(n)]
+    parts = {}
+    with mp.get_context("spawn").Pool(n) as pool:
+        for res in pool.map(_oracle_cut_parts, [(d, c) for c in chunks]):
+            parts.update(res)
+    return d, parts
+
+
 def oracle_dt(disc, factor=0.9):
     return factor * eigen.dt_crit(eigen.dense_lambda_max(disc.K, disc.ML))
 
