@@ -401,6 +401,24 @@ class Discretization:
                              shape=(len(np.atleast_2d(pts)) * self.ncomp, self.n_dof))
 
     # ---------------------------------------------------------------- IMEX partition
+    def explicit_block(self):
+        """(K_dd, M_L on d, d indices): the explicit block of the IMEX partition (Sec. 2.6).
+        A d-DOF has support in uncut cells only, so its rows of K and of the lumped mass
+        are sums of the reference stiffness and the GLL mass of those cells; no cut-cell
+        integral is needed."""
+        c = np.zeros(self.n_dof, dtype=bool)
+        c[self.c_dofs()] = True
+        nl = self.n_loc
+        ii, jj = np.meshgrid(np.arange(nl), np.arange(nl), indexing="ij")
+        D = np.stack([self.elem_dofs[e] for e in self.uncut])
+        K = sp.csr_matrix((np.tile(self.K_ref.ravel(), len(self.uncut)),
+                           (D[:, ii.ravel()].ravel(), D[:, jj.ravel()].ravel())),
+                          shape=(self.n_dof, self.n_dof))
+        ml = np.zeros(self.n_dof)
+        np.add.at(ml, D.ravel(), np.tile(self.m_gll, len(self.uncut)))
+        d = np.nonzero(~c)[0]
+        return K[d][:, d], ml[d], d
+
     def c_dofs(self, all_dofs=False):
         """DOFs with support in at least one cut cell (Sec. 2.6)."""
         if all_dofs:

@@ -6,12 +6,15 @@
   v_i = 1 + 0.5 sin(i) over the DOFs (i = global DOF number), stop when
   |lambda_k - lambda_{k-1}| <= rtol lambda_k or after max_iter products.
   It returns a lower bound of lambda_max (an upper bound of dt_crit).
+* ``lanczos_lambda_max``  - the largest eigenvalue of M^{-1/2} K M^{-1/2} by ARPACK's
+  Lanczos iteration (scipy), for diagonal M on grids too large for the dense solver.
 * ``element_bound``      - max_e lambda_max(K^e, M_L^e), an upper bound of the global
   lambda_max for a diagonal mass assembled from element diagonals.
 
 Pins: power iteration converges to the dense value on tiny grids, the dense value sits
 below the element bound, and CDM is stable at 0.99 dt_crit and unstable at 1.01 dt_crit
-(tests/test_oracle_eigen.py).
+(tests/test_oracle_eigen.py); the critical steps of the IMEX explicit block on the paper's
+rotated cube equal the paper's for p = 2 to 5 (tests/test_oracle_imex_dt_table.py).
 """
 from __future__ import annotations
 
@@ -27,6 +30,14 @@ def dense_lambda_max(K, ML):
     s = 1.0 / np.sqrt(ML)
     A = s[:, None] * K.toarray() * s[None, :]
     return sla.eigvalsh(A).max()
+
+
+def lanczos_lambda_max(K, ML):
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    s = 1.0 / np.sqrt(ML)
+    A = sp.diags(s) @ K @ sp.diags(s)
+    return float(spla.eigsh(A, k=1, which="LA", tol=1e-13, v0=start_vector(A.shape[0]))[0][0])
 
 
 def start_vector(n):
