@@ -339,17 +339,31 @@ def run_ours(args, rank, world, local_rank):
         s.sync()
         run_s = time.perf_counter() - t0
         u_end, _ = s.get_state()
+        # observer series of the run (the ring holds w.steps + 1 rows)
+        series = s.sample(run_steps + 1) if run_steps <= w.steps else None
         results[prec] = dict(step_ms=step_ms, kernels=kernels, steady_ms=steady_ms, info=info,
-                             clocks=clk, run_s=run_s, u_end=u_end, solver=s, wall=t_wall, dt=dt,
+                             clocks=clk, run_s=run_s, u_end=u_end, series=series, solver=s, wall=t_wall, dt=dt,
                              run_steps=run_steps, scheme=wv.scheme, stab=wv.stab,
                              tile=None if tile is None else {"variant": tile[0], "cells": list(s.info().tile),
                                                               "autotune_ms_per_apply": [float(x) for x in tile[1]]})
         if prec == "fp64":
             ref_state = u_end
+    from paper_2501_19013_gb300.metrics import observer_error
     for prec, r in results.items():
+        r["e_obs"] = None
         if ref_state is not None and r["scheme"] == "cdm" and r["stab"] == results["fp64"]["stab"]:
             nr = np.linalg.norm(ref_state)
             r["rel_l2"] = float(np.linalg.norm(r["u_end"] - ref_state) / nr) if nr > 0 else 0.0
+            ref_series = results["fp64"]["series"]
+            if (r["series"] is not None and ref_series is not None and r["series"].shape == ref_series.shape
+                    and r["series"].shape[0] > 1):
+                n = r["series"].shape[0] - 1
+                nc = r["info"].ncomp
+                r["e_obs"] = {"e_100": observer_error(r["series"], ref_series, min(100, n), nc),
+                              f"e_{n}": observer_error(r["series"], ref_series, n, nc),
+                              "definition": "Eq. error: mean over observers of the relative L2 error "
+                                            "of the observer series at n_s equidistant instants, "
+                                            "against the FP64 path"}
         else:
             r["rel_l2"] = None
     # headline: fastest variant that reaches rel-L2 <= 1e-4 against FP64
@@ -415,6 +429,7 @@ def run_ours(args, rank, world, local_rank):
         variants_out[p] = {"dof_steps_per_s": r["info"].n_dof / (r["step_ms"] * 1e-3),
                            "ms_per_step": r["step_ms"], "steady_state_ms_per_step": r["steady_ms"],
                            "rel_l2_vs_fp64_after_run": r["rel_l2"],
+                           "observer_error_vs_fp64": r["e_obs"],
                            "run_steps": r["run_steps"], "dt": r["dt"], "scheme": r["scheme"],
                            "stab": r["stab"], "run_wall_s": r["run_s"],
                            "time_to_accuracy_s": (r["step_ms"] * 1e-3 * r["run_steps"]) if (r["rel_l2"] is not None and r["rel_l2"] <= 1e-4) else None,
