@@ -11,28 +11,6 @@ def oracle_disc(w, **kw):
     return OD.from_workload(w, **kw)
 
 
-def _oracle_cut_cells(args):
-    d, cells = args
-    for e in cells:
-        d._cut_matrices(e)
-    return {e: (d.K_cut[e], d.M_cut_cons[e], d.M_cut_stab[e], d.ml_cut[e], d.scale_cut[e]) for e in cells}
-
-
-def oracle_disc_parallel(w, workers=None):
-    """The oracle's discretisation of ``w`` with its cut cells integrated by a pool of
-    spawned processes (each cell by the oracle's own code), then assembled."""
-    import multiprocessing as mp
-    d = OD.from_workload(w, assemble=False)
-    n = max(1, min(workers or os.cpu_count() or 1, 8, len(d.cut)))
-    chunks = [list(d.cut)[i::n] for i in range(n)]
-    with mp.get_context("spawn").Pool(n) as pool:
-        for res in pool.map(_oracle_cut_cells, [(d, c) for c in chunks]):
-            for e, (K, Mc, Ms, ml, sc) in res.items():
-                d.K_cut[e], d.M_cut_cons[e], d.M_cut_stab[e], d.ml_cut[e], d.scale_cut[e] = K, Mc, Ms, ml, sc
-    d._assemble()
-    return d
-
-
 def _oracle_cut_parts(args):
     from oracle.quadrature import cut_cell_quadrature
     d, cells = args
