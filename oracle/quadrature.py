@@ -11,8 +11,8 @@ integrands of a leaf with constant indicator).
 Pins: sum of weights times indicator against the closed-form area of a disk / circular
 segment inside a box (error shrinking with depth), exact voxel volumes at depth 1, and
 equality with the plain GL rule for uncut cells (tests/test_oracle_quadrature.py); with
-depth p + 1, three of the paper's critical time steps of the consistent-mass CDM on the
-rotated cube (p = 3, ne = 13; tests/test_timing_table_cpu.py).
+depth p + 1, five of the paper's critical time steps of the consistent-mass CDM on the
+rotated cube (p = 2, ne = 28 and p = 3, ne = 13; tests/test_timing_table_cpu.py).
 """
 from __future__ import annotations
 

@@ -1,9 +1,10 @@
-"""The paper's critical time steps of the consistent-mass CDM on the rotated cube at p = 3,
-ne = 13 (golden values in tests/golden/timing_table_p3_ne13_dt_crit.txt), on the CPU.
+"""The paper's critical time steps of the consistent-mass CDM on the rotated cube (golden
+values in tests/golden/timing_table_cpu_dt_crit.txt: p = 2, ne = 28 and p = 3, ne = 13),
+on the CPU.
 
 The oracle's discretisation (its cut cells integrated in a process pool, split into the
-physical and the fictitious part so that one integration serves every alpha) gives the
-alpha-stabilised rows (eps = 0) and the eigenvalue-stabilised row (Sec. 2.5); the
+physical and the fictitious part so that one integration per grid serves every alpha)
+gives the alpha-stabilised rows (eps = 0) and the eigenvalue-stabilised row (Sec. 2.5); the
 library's host setup (element stiffnesses and consistent element masses through
 ``ibfem_get_element_mass``) gives the eigenvalue-stabilised row.  Each assembles K and the
 consistent mass M (GLL diagonal in uncut cells, Sec. 2.4); the largest eigenvalue of
@@ -26,22 +27,25 @@ from paper_2501_19013_gb300 import workloads as W
 
 ib = pytest.importorskip("paper_2501_19013_gb300.ibfem")
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "timing_table_p3_ne13_dt_crit.txt")
-P, NE = 3, 13
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "timing_table_cpu_dt_crit.txt")
 
 
 def rows():
     out = []
     for line in open(GOLDEN):
         if line.strip() and not line.startswith("#"):
-            a, eps, dt = line.split()
-            out.append((float(a), float(eps), float(dt) * 1e-3))
+            p, ne, a, eps, dt = line.split()
+            out.append((int(p), int(ne), float(a), float(eps), float(dt) * 1e-3))
     return out
 
 
-def cube(alpha, eps):
-    return W.rotated_cube(ne=NE, p=P, alpha=alpha, stab="evs" if eps > 0 else "none", eps=eps,
-                          quad_depth=P + 1)
+def grids():
+    return sorted({(p, ne) for p, ne, _, _, _ in rows()})
+
+
+def cube(p, ne, alpha, eps):
+    return W.rotated_cube(ne=ne, p=p, alpha=alpha, stab="evs" if eps > 0 else "none", eps=eps,
+                          quad_depth=p + 1)
 
 
 def dt_crit(K, M):
@@ -51,16 +55,18 @@ def dt_crit(K, M):
     return 2.0 / np.sqrt(lam)
 
 
-@pytest.fixture(scope="module")
-def oracle_parts():
+@pytest.fixture(scope="module", params=grids(), ids=lambda g: f"p{g[0]}_ne{g[1]}")
+def oracle_parts(request):
     from helpers import oracle_cut_parts
-    return oracle_cut_parts(cube(1e-8, 0.0))
+    p, ne = request.param
+    d, parts = oracle_cut_parts(cube(p, ne, 1e-8, 0.0))
+    return p, ne, d, parts
 
 
 def test_oracle_dt_crit_matches_the_paper(oracle_parts):
-    d, parts = oracle_parts
+    p, ne, d, parts = oracle_parts
     assert d.f_lambda == 1e-2
-    for alpha, eps, dt_paper in rows():
+    for alpha, eps, dt_paper in [r[2:] for r in rows() if r[:2] == (p, ne)]:
         d.eps, d.stab, d.alpha = eps, ("evs" if eps > 0 else "none"), alpha
         for e, (Kp, Mp, Kf, Mf) in parts.items():
             Mo = Mp + alpha * Mf
@@ -69,15 +75,15 @@ def test_oracle_dt_crit_matches_the_paper(oracle_parts):
             d.ml_cut[e], d.scale_cut[e] = hrz(Ms), 1.0
         d._assemble()
         dt = dt_crit(d.K, d.consistent_mass(stabilised=True))
-        assert abs(dt - dt_paper) <= 2e-4 * dt_paper, (alpha, eps, dt, dt_paper)   # four digits
+        assert abs(dt - dt_paper) <= 2e-4 * dt_paper, (p, ne, alpha, eps, dt, dt_paper)   # four digits
 
 
 def test_oracle_split_integrals_equal_the_direct_ones(oracle_parts):
     """K_phys + alpha K_fict equals the oracle's direct integration at that alpha."""
-    d, parts = oracle_parts
-    w = cube(1e-4, 0.0)
+    p, ne, d, parts = oracle_parts
+    w = cube(p, ne, 1e-4, 0.0)
     dd = OD.from_workload(w, assemble=False)
-    for e in list(parts)[::60]:
+    for e in list(parts)[:: max(1, len(parts) // 8)]:
         dd._cut_matrices(e)
         Kp, Mp, Kf, Mf = parts[e]
         np.testing.assert_allclose(Kp + 1e-4 * Kf, dd.K_cut[e], rtol=1e-12, atol=1e-12 * np.abs(dd.K_cut[e]).max())
@@ -105,9 +111,9 @@ def assembled(s, d):
             sp.csr_matrix((np.concatenate(vm), (r, c)), shape=(n, n)))
 
 
-@pytest.mark.parametrize("alpha,eps,dt_paper", [r for r in rows() if r[1] > 0])
-def test_host_setup_evs_dt_crit_matches_the_paper(alpha, eps, dt_paper):
-    w = cube(alpha, eps)
+@pytest.mark.parametrize("p,ne,alpha,eps,dt_paper", [r for r in rows() if r[3] > 0])
+def test_host_setup_evs_dt_crit_matches_the_paper(p, ne, alpha, eps, dt_paper):
+    w = cube(p, ne, alpha, eps)
     s = ib.from_workload(w, host_only=True, scheme="cdm_consistent")
     d = OD.from_workload(w, assemble=False)      # classes and DOF numbering only
     assert s.info().n_dof == d.n_dof
