@@ -246,6 +246,29 @@ def build_solver(w, precision, stream):
     return s
 
 
+def accuracy_against_fp64(results):
+    """Per variant against the FP64 path of the same scheme and stabilisation: the relative
+    L2 error of the final field (``rel_l2``) and the paper's observer error (Eq. error:
+    e_100 and e_N over all N steps, ``e_obs``); None where there is no comparable FP64 run."""
+    from paper_2501_19013_gb300.metrics import observer_error
+    ref = results.get("fp64")
+    for r in results.values():
+        r["rel_l2"], r["e_obs"] = None, None
+        if ref is None or r["scheme"] != "cdm" or r["stab"] != ref["stab"]:
+            continue
+        nr = np.linalg.norm(ref["u_end"])
+        r["rel_l2"] = float(np.linalg.norm(r["u_end"] - ref["u_end"]) / nr) if nr > 0 else 0.0
+        a, b = r.get("series"), ref.get("series")
+        if a is not None and b is not None and a.shape == b.shape and a.shape[0] > 1:
+            n = a.shape[0] - 1
+            nc = r["info"].ncomp
+            r["e_obs"] = {"e_100": observer_error(a, b, min(100, n), nc),
+                          f"e_{n}": observer_error(a, b, n, nc),
+                          "definition": "Eq. error: mean over observers of the relative L2 error "
+                                        "of the observer series at n_s equidistant instants, "
+                                        "against the FP64 path"}
+
+
 def aggregate_replicas(step_ms, n_dof, world, device=None):
     """Replicas: every rank advances its own copy of the workload.  The job's step time is
     the slowest rank's; the job's throughput counts the DOFs of all ranks."""
@@ -290,7 +313,6 @@ def run_ours(args, rank, world, local_rank):
 
     variants = [v for v in args.precisions.split(",") if v]
     results = {}
-    ref_state = None
     dts = {}
     for prec in variants:
         wv, pv = parse_variant(prec, w)
@@ -346,26 +368,7 @@ def run_ours(args, rank, world, local_rank):
                              run_steps=run_steps, scheme=wv.scheme, stab=wv.stab,
                              tile=None if tile is None else {"variant": tile[0], "cells": list(s.info().tile),
                                                               "autotune_ms_per_apply": [float(x) for x in tile[1]]})
-        if prec == "fp64":
-            ref_state = u_end
-    from paper_2501_19013_gb300.metrics import observer_error
-    for prec, r in results.items():
-        r["e_obs"] = None
-        if ref_state is not None and r["scheme"] == "cdm" and r["stab"] == results["fp64"]["stab"]:
-            nr = np.linalg.norm(ref_state)
-            r["rel_l2"] = float(np.linalg.norm(r["u_end"] - ref_state) / nr) if nr > 0 else 0.0
-            ref_series = results["fp64"]["series"]
-            if (r["series"] is not None and ref_series is not None and r["series"].shape == ref_series.shape
-                    and r["series"].shape[0] > 1):
-                n = r["series"].shape[0] - 1
-                nc = r["info"].ncomp
-                r["e_obs"] = {"e_100": observer_error(r["series"], ref_series, min(100, n), nc),
-                              f"e_{n}": observer_error(r["series"], ref_series, n, nc),
-                              "definition": "Eq. error: mean over observers of the relative L2 error "
-                                            "of the observer series at n_s equidistant instants, "
-                                            "against the FP64 path"}
-        else:
-            r["rel_l2"] = None
+    accuracy_against_fp64(results)
     # headline: fastest variant that reaches rel-L2 <= 1e-4 against FP64
     qual = {p: r for p, r in results.items() if r["rel_l2"] is not None and r["rel_l2"] <= 1e-4}
     best = min(qual, key=lambda p: qual[p]["step_ms"]) if qual else variants[0]

@@ -42,3 +42,31 @@ def test_single_rank_aggregation():
     import bench
     step_ms, value = bench.aggregate_replicas(2.0, 1000, 1)
     assert step_ms == 2.0 and value == pytest.approx(1000 / 2e-3)
+
+
+def test_accuracy_against_fp64_on_fake_runs():
+    """The bench's accuracy table: final-field rel-L2 and the observer error e_100 / e_N
+    of each comparable variant against the FP64 path; none for another scheme."""
+    import numpy as np
+    import bench
+
+    class Info:
+        ncomp = 2
+
+    t = np.linspace(0.0, 1.0, 1001)
+    ref = np.stack([np.sin(5 * t + i) for i in range(6)], axis=1)
+    u = np.linspace(1.0, 2.0, 50)
+    results = {
+        "fp64": dict(scheme="cdm", stab="evs", u_end=u, series=ref, info=Info()),
+        "exact": dict(scheme="cdm", stab="evs", u_end=u * (1 + 3e-6), series=ref * (1 + 2e-6), info=Info()),
+        "imex": dict(scheme="imex", stab="none", u_end=u, series=ref, info=Info()),
+    }
+    bench.accuracy_against_fp64(results)
+    assert results["fp64"]["rel_l2"] == 0.0 and results["fp64"]["e_obs"]["e_100"] == 0.0
+    assert abs(results["exact"]["rel_l2"] - 3e-6) < 1e-12
+    assert abs(results["exact"]["e_obs"]["e_100"] - 2e-6) < 1e-12
+    assert abs(results["exact"]["e_obs"]["e_1000"] - 2e-6) < 1e-12
+    assert results["imex"]["rel_l2"] is None and results["imex"]["e_obs"] is None
+    del results["fp64"]
+    bench.accuracy_against_fp64(results)
+    assert results["exact"]["rel_l2"] is None
