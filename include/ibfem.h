@@ -175,6 +175,9 @@ int ibfem_destroy(ibfem_t* h);
 /* Message of the last failed call on this thread ("" if none).  Valid until the next
  * failing call on the same thread. */
 const char* ibfem_last_error(void);
+/* Fill *out with the handle's sizes, counts, step, time and device footprint (the fields
+ * of ibfem_info_t).  Host data only: no synchronisation, valid for host_only handles and
+ * batch members.  Errors: ARG (null h or out).                                          */
 int ibfem_info(const ibfem_t* h, ibfem_info_t* out);
 
 /* ---- problem data ---------------------------------------------------------------- */

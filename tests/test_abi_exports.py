@@ -40,3 +40,28 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(ibfem, "LIB_PATH", str(tmp_path / "libibfem.so"))
     with pytest.raises(ImportError):
         ibfem.lib()
+
+
+# declarations documented by the comment of the declaration right above them
+GROUPED = {"ibfem_autotune": "ibfem_set_tile_variant"}
+
+
+def test_every_entry_point_is_documented():
+    """Each declaration in include/ is preceded by its comment (GROUPED: shares the comment
+    of the declaration right above it)."""
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", f)).read().splitlines()
+        decl = re.compile(r"^\s*(?:int|const char\*)\s+(ibfem_\w+)\s*\(")
+        for i, line in enumerate(lines):
+            m = decl.match(line)
+            if not m:
+                continue
+            j = i - 1
+            while j >= 0 and not lines[j].strip():
+                j -= 1
+            prev = lines[j].strip()
+            pm = decl.match(lines[j])
+            grouped = pm is not None and GROUPED.get(m.group(1)) == pm.group(1)
+            assert prev.endswith("*/") or grouped, m.group(1)
