@@ -28,6 +28,13 @@
  *  - ibfem_step only enqueues work on the handle's stream; ibfem_sample, ibfem_get_state,
  *    ibfem_crit_dt, ibfem_sync and the other "read" calls synchronise that stream.
  *  - Handles are not thread-safe; distinct handles may be used from distinct threads.
+ *  - Every call that works on the device also returns ARG for a null handle, STATE for
+ *    a host_only handle or a batch member (ibfem_info and ibfem_destroy excepted), CUDA
+ *    when a CUDA call fails and OOM when an allocation fails; the per-function "Errors"
+ *    lists add what is particular to the call.
+ *  - Entry points marked "library" (lifetime, diagnostics, timing, batching, tile shape,
+ *    deferred upload) serve the GPU runtime; the paper, a one-process CPU study, has no
+ *    counterpart for them.
  */
 #ifndef IBFEM_H
 #define IBFEM_H
@@ -169,15 +176,16 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry,
  * Errors: ARG (null argument; src solves a c-set, i.e. IMEX or the consistent-mass CDM
  * with cut cells), STATE (src is host_only), OOM, CUDA.                               */
 int ibfem_clone(ibfem_t* src, ibfem_t** out);
-/* Free every resource of the handle (NULL is accepted).  Arrays shared with clones
- * are freed with the last handle that uses them. */
+/* Library.  Free every resource of the handle (NULL is accepted; waits for the handle's
+ * queued work, and for its batch's if it is a member).  Arrays shared with clones are
+ * freed with the last handle that uses them.  Always returns IBFEM_OK.                 */
 int ibfem_destroy(ibfem_t* h);
-/* Message of the last failed call on this thread ("" if none).  Valid until the next
- * failing call on the same thread. */
+/* Library.  Message of the last failed call on this thread ("" if none).  Valid until
+ * the next failing call on the same thread.                                             */
 const char* ibfem_last_error(void);
-/* Fill *out with the handle's sizes, counts, step, time and device footprint (the fields
- * of ibfem_info_t).  Host data only: no synchronisation, valid for host_only handles and
- * batch members.  Errors: ARG (null h or out).                                          */
+/* Library.  Fill *out with the handle's sizes, counts, step, time and device footprint
+ * (the fields of ibfem_info_t).  Host data only: no synchronisation, valid for host_only
+ * handles and batch members.  Errors: ARG (null h or out).                              */
 int ibfem_info(const ibfem_t* h, ibfem_info_t* out);
 
 /* ---- problem data ---------------------------------------------------------------- */
@@ -199,7 +207,10 @@ int ibfem_set_observers(ibfem_t* h, int npts, const double* xyz, int64_t capacit
 
 /* Initial state Psi_0, Psi'_0 (host, kept-DOF order, n_dof each; NULL = zero).  The
  * start-up value u^{-1} = u^0 - dt v^0 + dt^2/2 M_L^{-1}(F^0 - K u^0) is formed on the
- * device (IMEX: its d-part, plus Psi''_0 on the c-part from M^cc).  Requires set_dt.   */
+ * device: the initialisation of Algorithm 1 with beta = 0 (the paper leaves the CDM
+ * start-up open); IMEX: its d-part, plus Psi''_0 = (M^cc)^{-1}(F^c_0 - K^c u_0) on the
+ * c-part (Algorithm 2 initialisation).  Resets the step count and the observer ring.
+ * Errors: STATE (set_dt not called).                                                    */
 int ibfem_set_initial(ibfem_t* h, const double* u0, const double* v0);
 
 /* Critical step dt_crit = 2 / sqrt(lambda_max(K, M_L)) (Sec. 2.3) by power iteration on
@@ -209,14 +220,18 @@ int ibfem_set_initial(ibfem_t* h, const double* u0, const double* v0);
 int ibfem_crit_dt(ibfem_t* h, int max_iter, double rtol, double* dt_crit,
                   double* lambda_max, int* iterations);
 
-/* Set the step size (> 0).  Rescales dt^2 M_L^{-1} on the device and, for IMEX,
- * refactors S = M^cc + dt^2/4 K^cc on the host.  Errors: ARG, EIG.                     */
+/* Set the step size dt of Eq. cdm (> 0, finite).  Rescales dt^2 M_L^{-1} on the device
+ * and, for IMEX, refactors S = M^cc + beta dt^2 K^cc (Algorithm 2, beta = 1/4) on the
+ * host.  Errors: ARG (dt not positive), EIG (factorisation failed).                     */
 int ibfem_set_dt(ibfem_t* h, double dt);
 
 /* ---- time stepping --------------------------------------------------------------- */
 
-/* Enqueue n steps (n >= 0) on the handle's stream, replaying a captured CUDA graph of
- * the per-step kernels.  Asynchronous.  Errors: STATE (no dt / initial), CUDA.         */
+/* Enqueue n time steps (n >= 0) on the handle's stream: Eq. cdm (IBFEM_CDM), Algorithm 2
+ * (IBFEM_IMEX) or Algorithm 2 with beta = 0 (IBFEM_CDM_CONSISTENT), replaying a captured
+ * CUDA graph of the per-step kernels.  Asynchronous: divergence and device timeouts are
+ * reported by the next synchronising call.  Errors: ARG (n < 0), STATE (no initial state:
+ * call set_initial or set_state first).                                                  */
 int ibfem_step(ibfem_t* h, int64_t n);
 
 /* Same as ibfem_step, but every kernel is launched directly with a pair of CUDA events
@@ -225,38 +240,53 @@ int ibfem_step(ibfem_t* h, int64_t n);
  * outside the timed events, to evict the L2 cache.  ms[0] accumulates the device time of
  * whole steps (first kernel start to last kernel end), ms[1 + k] that of kernel k (at most
  * max_slots values; names from ibfem_kernel_name); *n_slots receives the slot count.
- * Synchronises.  Meant for benchmarks and profiles.                                    */
+ * Synchronises.  Library: meant for benchmarks and profiles.
+ * Errors: ARG (n < 0, null ms with max_slots > 0, null flush_buf with flush_bytes > 0),
+ * STATE (no initial state).                                                             */
 int ibfem_step_timed(ibfem_t* h, int64_t n, void* flush_buf, size_t flush_bytes, double* ms,
                      int max_slots, int* n_slots);
-/* Name of kernel slot `slot` of ibfem_step_timed ("" if out of range). */
+/* Library.  Name of kernel slot `slot` of ibfem_step_timed ("" if out of range or for a
+ * null handle); the string lives as long as the library.                               */
 const char* ibfem_kernel_name(const ibfem_t* h, int slot);
 
-/* Synchronise the stream; report a tensor-core kernel whose bounded wait (an mbarrier of
- * the MMA or of the K_ref copy) gave up as IBFEM_ERR_TIMEOUT, and a non-finite state as
- * IBFEM_ERR_DIVERGED.  The flags stay set (the state is no longer trustworthy). */
+/* Library.  Synchronise the stream; report a tensor-core kernel whose bounded wait (an
+ * mbarrier of the MMA or of the K_ref copy) gave up as IBFEM_ERR_TIMEOUT, and a non-finite
+ * state (a run beyond the stability limit of Sec. 2.3) as IBFEM_ERR_DIVERGED.  The flags
+ * stay set (the state is no longer trustworthy).                                        */
 int ibfem_sync(ibfem_t* h);
 
-/* Observer series recorded since set_observers/set_initial, oldest first: up to
- * max_rows rows of npts*ncomp doubles (row r = time t_{k0+r}).  The last row is the
- * current state Psi(t_k).  *rows receives the count.  Synchronises.                    */
+/* Observer series (Sec. 3.2) recorded since set_observers/set_initial, oldest first: up
+ * to max_rows rows of npts*ncomp doubles (row r = time t_{k0+r}).  The last row is the
+ * current state Psi(t_k).  *rows receives the count.  Synchronises.
+ * Errors: ARG (null out or rows, max_rows < 0), DIVERGED, TIMEOUT (as ibfem_sync).     */
 int ibfem_sample(ibfem_t* h, int64_t max_rows, double* out, int64_t* rows);
 
-/* State (host, kept-DOF order, n_dof each; either pointer may be NULL). Synchronises.
- * CDM: u = u^k, u_prev = u^{k-1}.  IMEX: u_prev holds u^{k-1} on d and Psi'^k on c.     */
+/* State of the integrator (host, kept-DOF order, n_dof each; either pointer may be NULL).
+ * Synchronises.  CDM (Eq. cdm): u = u^k, u_prev = u^{k-1}.  IMEX (Algorithm 2): u_prev
+ * holds u^{k-1} on d and Psi'^k on c.                                                    */
 int ibfem_get_state(ibfem_t* h, double* u, double* u_prev);
-/* Restore a state previously read by ibfem_get_state together with its step index. */
+/* Restore a state previously read by ibfem_get_state together with its step index (the
+ * load f_t(t_k) of the next step follows from it).  Continuing from it is bitwise equal
+ * to not having stopped.  Errors: ARG (null u or u_prev, step < 0), STATE (no dt).       */
 int ibfem_set_state(ibfem_t* h, const double* u, const double* u_prev, int64_t step);
 
 /* ---- inspection (used by the parity tests) ---------------------------------------- */
 
-/* y = K x with x, y in kept-DOF order (host).  Synchronises. */
+/* y = K x (K of Eq. semi, applied element by element: the shared reference matrix in
+ * uncut cells, the space-tree integrated K^e in cut cells, Sec. 2.2), x and y host
+ * vectors in kept-DOF order.  Synchronises.  Errors: ARG (null x or y).                   */
 int ibfem_apply_operator(ibfem_t* h, const double* x, double* y);
-/* Assembled lumped mass diagonal M_L (kept-DOF order, n_dof doubles). */
+/* Assembled lumped mass diagonal M_L of Eq. cdm (Sec. 2.4: GLL in uncut cells, HRZ
+ * diagonal scaling of the (stabilised) cut-cell mass), kept-DOF order, n_dof doubles.
+ * Host data.  Errors: ARG (null argument).                                               */
 int ibfem_get_lumped_mass(ibfem_t* h, double* ml);
-/* Flat indices (x fastest) of the cut cells, n_cut int64 values in ascending order. */
+/* Flat indices (x fastest) of the cut cells (Sec. 2.2: cells the immersed boundary
+ * crosses), n_cut int64 values in ascending order.  Host data.  Errors: ARG (null).      */
 int ibfem_get_cut_cells(ibfem_t* h, int64_t* cells);
-/* Element stiffness (n_loc x n_loc, row-major) used for cell `cell` (shared reference
- * matrix for uncut cells); optional lumped diagonal (n_loc). Errors: ARG (outside).   */
+/* Element stiffness (n_loc x n_loc, row-major) used for cell `cell`: the shared reference
+ * matrix for uncut cells, the alpha^FCM-weighted space-tree integral for cut cells (Sec.
+ * 2.2, Eq. weak_form_extended); optional lumped diagonal (n_loc, Sec. 2.4).  Host data.
+ * Errors: ARG (cell outside or out of range).                                            */
 int ibfem_get_element(ibfem_t* h, int64_t cell, double* K, double* ml);
 /* Consistent element mass (n_loc x n_loc, row-major) of cell `cell` as the consistent-mass
  * schemes use it: for a cut cell the alpha-integrated space-tree mass M^o (Sec. 2.2), plus
@@ -309,7 +339,7 @@ int ibfem_upload(ibfem_t* h);
 typedef struct ibfem_batch_s ibfem_batch_t;
 
 /* New empty batch on `device`; `stream` (cudaStream_t, NULL = a private stream) carries
- * its work.  Errors: CUDA.                                                              */
+ * its work.  Errors: ARG (null out), CUDA.                                              */
 int ibfem_batch_create(void* stream, int device, ibfem_batch_t** out);
 
 /* Admit handle h for n_steps (>= 1) more steps.  The batch's work starts after everything
@@ -321,14 +351,17 @@ int ibfem_batch_add(ibfem_batch_t* b, ibfem_t* h, int64_t n_steps);
 /* Enqueue n batched steps (asynchronous).  A member whose budget runs out inside the n
  * steps stops there exactly (its tiles are skipped afterwards) and becomes "finished":
  * it leaves the batch, and its own stream is ordered after the batch work queued so far,
- * so that ibfem_sample / get_state on it see its final state.  Errors: CUDA.             */
+ * so that ibfem_sample / get_state on it see its final state.  Errors: ARG (null batch,
+ * n < 0), CUDA.                                                                         */
 int ibfem_batch_run(ibfem_batch_t* b, int64_t n);
 
 /* Hand back up to max_done finished handles (in completion order) in done[]; *n_done
- * receives their count.  The handles are ordinary handles again (the caller owns them).  */
+ * receives their count.  The handles are ordinary handles again (the caller owns them).
+ * Errors: ARG (null b or n_done, or null done with max_done > 0).                         */
 int ibfem_batch_poll(ibfem_batch_t* b, ibfem_t** done, int max_done, int* n_done);
 
-/* Members still stepping, finished members not yet polled, batched steps enqueued.      */
+/* Members still stepping, finished members not yet polled, batched steps enqueued (any
+ * output may be NULL).  Errors: ARG (null batch).                                        */
 int ibfem_batch_status(const ibfem_batch_t* b, int* n_active, int* n_finished, int64_t* steps_enqueued);
 
 /* Block until at most max_pending enqueued chunks (ibfem_batch_run calls are split into
@@ -340,7 +373,7 @@ int ibfem_batch_wait(ibfem_batch_t* b, int max_pending);
 int ibfem_batch_sync(ibfem_batch_t* b);
 
 /* Wait for the queued work, release members still in the batch (at the step their device
- * counter reached) and free the batch.                                                   */
+ * counter reached) and free the batch (NULL is accepted).  Always returns IBFEM_OK.       */
 int ibfem_batch_destroy(ibfem_batch_t* b);
 
 /* ---- allocation-free operator ----------------------------------------------------- */
