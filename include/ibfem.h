@@ -163,7 +163,7 @@ typedef struct {
 int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry,
                  double alpha, const ibfem_stab* stab, const ibfem_options* opt,
                  ibfem_t** out);
-/* Several loads on one discretisation (shared-geometry multi-source runs).  *out
+/* Library.  Several loads on one discretisation (shared-geometry multi-source runs).  *out
  * receives a new handle on the same grid, geometry, material, scheme, precision and
  * tile shape as `src`, whose device geometry, cut-cell matrices, reference stiffness
  * and tensor-core K_ref image it shares instead of holding a copy; it owns its state,
@@ -265,8 +265,9 @@ int ibfem_sample(ibfem_t* h, int64_t max_rows, double* out, int64_t* rows);
  * Synchronises.  CDM (Eq. cdm): u = u^k, u_prev = u^{k-1}.  IMEX (Algorithm 2): u_prev
  * holds u^{k-1} on d and Psi'^k on c.                                                    */
 int ibfem_get_state(ibfem_t* h, double* u, double* u_prev);
-/* Restore a state previously read by ibfem_get_state together with its step index (the
- * load f_t(t_k) of the next step follows from it).  Continuing from it is bitwise equal
+/* Restore a state previously read by ibfem_get_state (the pair of Eq. cdm, or of
+ * Algorithm 2 for IMEX) together with its step index (the load f_t(t_k) of the next step
+ * follows from it).  Continuing from it is bitwise equal
  * to not having stopped.  Errors: ARG (null u or u_prev, step < 0), STATE (no dt).       */
 int ibfem_set_state(ibfem_t* h, const double* u, const double* u_prev, int64_t step);
 
