@@ -20,6 +20,15 @@ f_s = exp(-|x - x_l|^2 / (2 sigma^2)).
 
 Observers (Sec. 3.2): Psi(x) = sum_j N_j(x) Psi_j in the lowest-numbered kept cell that
 contains x.
+
+Pins: the element-by-element K u equals the assembled product, source vectors sum to the
+wavelet (partition of unity) and observers interpolate polynomials exactly
+(tests/test_oracle_integrators.py); the Gaussian load's integral, centre and alpha
+weighting (tests/test_oracle_gauss_load.py); the DOF counts of the paper's rotated cube
+(tests/test_oracle_geometry.py); the explicit block of the IMEX partition gives the
+paper's IMEX critical time steps for p = 2 to 5 (tests/test_oracle_imex_dt_table.py) and
+the assembled consistent mass its consistent-mass ones at p = 2 and 3
+(tests/test_timing_table_cpu.py).
 """
 from __future__ import annotations
 
