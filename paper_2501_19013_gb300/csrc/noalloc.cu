@@ -56,10 +56,12 @@ extern "C" int ibfem_apply_operator_noalloc(int dim, int p, int ncomp, const int
     nn_loc *= p + 1;
   }
   const int n_loc = nn_loc * ncomp;
-  if (n_cut * (long long)n_loc > kScratchDoubles)
+  // n_cut * n_loc <= kScratchDoubles, written as a division so that no product can overflow
+  if (n_cut > kScratchDoubles / n_loc)
     return noalloc_fail(IBFEM_ERR_ARG,
-                        "ibfem_apply_operator_noalloc: n_cut * n_loc = " + std::to_string(n_cut * (long long)n_loc) +
-                            " exceeds the static scratch of " + std::to_string(kScratchDoubles) + " doubles");
+                        "ibfem_apply_operator_noalloc: n_cut = " + std::to_string(n_cut) + " cut cells of " +
+                            std::to_string(n_loc) + " DOFs exceed the static scratch of " +
+                            std::to_string(kScratchDoubles) + " doubles");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(IBFEM_ERR_CUDA, cudaGetErrorString(e));

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from helpers import SMALL_CASES, gpu_solver, rel_l2
+from paper_2501_19013_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -52,20 +53,30 @@ def _inputs(s, w):
                 K_cut=K_cut, n_lat_dof=int(np.prod(lat)) * nc, kept_dofs=kept_dofs)
 
 
-def test_noalloc_operator_matches_allocating_operator_twice():
+NO_CUT = lambda: W.plate_one_hole().with_(holes=None, name="plate_16x16_p2_no_holes")
+
+
+@pytest.mark.parametrize("case", ["elastic_evs_ragged", "voxel_3d_evs", "no_cut_cells"])
+def test_noalloc_operator_matches_allocating_operator_twice(case):
+    """2D plane strain with cut cells, 3D scalar with cut cells, and a grid with no cut cell
+    (null cut arrays: the cut-cell kernel is not launched)."""
     import torch
     from paper_2501_19013_gb300 import ibfem as ib
 
-    w = SMALL_CASES["elastic_evs_ragged"]()
+    w = NO_CUT() if case == "no_cut_cells" else SMALL_CASES[case]()
     s = gpu_solver(w)
     d = _inputs(s, w)
     dev = torch.device("cuda", 0)
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     cls = t(d["cls"], torch.uint8)
     cut_index = t(d["cut_index"], torch.int32)
-    cut = t(d["cut"].astype(np.int64), torch.int64)
     K_ref = t(d["K_ref"], torch.float64)
-    K_cut = t(d["K_cut"], torch.float64)
+    if len(d["cut"]):
+        cut = t(d["cut"].astype(np.int64), torch.int64)
+        K_cut = t(d["K_cut"], torch.float64)
+        cut_ptr, kcut_ptr = cut.data_ptr(), K_cut.data_ptr()
+    else:
+        cut_ptr, kcut_ptr = None, None      # no cut cells: the cut arrays may be null
     rng = np.random.default_rng(11)
     for call in range(2):      # two calls in a row share (and reuse) the static scratch
         x = rng.standard_normal(s.n_dof) * (1.0 + call)
@@ -76,8 +87,8 @@ def test_noalloc_operator_matches_allocating_operator_twice():
         yd = torch.full((d["n_lat_dof"],), float("nan"), dtype=torch.float64, device=dev)
         stream = torch.cuda.current_stream(dev)
         ib.apply_operator_noalloc(d["dim"], d["p"], d["nc"], d["n"], cls.data_ptr(),
-                                  cut_index.data_ptr(), cut.data_ptr(), len(d["cut"]),
-                                  K_ref.data_ptr(), K_cut.data_ptr(), xd.data_ptr(), yd.data_ptr(),
+                                  cut_index.data_ptr(), cut_ptr, len(d["cut"]),
+                                  K_ref.data_ptr(), kcut_ptr, xd.data_ptr(), yd.data_ptr(),
                                   stream.cuda_stream)
         torch.cuda.synchronize()
         y = yd.cpu().numpy()[d["kept_dofs"]]
@@ -91,4 +102,4 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         # 2^19 cut cells of 9 DOFs exceed the static scratch; rejected before any launch
         ib.apply_operator_noalloc(2, 2, 1, [1024, 1024], 1, 1, 1, 1 << 19, 1, 1, 1, 1, None)
     assert err.value.code == ib.ERR_ARG
-    assert "exceeds the static scratch" in str(err.value)
+    assert "the static scratch" in str(err.value)
