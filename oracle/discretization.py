@@ -54,7 +54,7 @@ def ricker(t, f_e):
 class Discretization:
     def __init__(self, dim, n, p, physics="scalar", geometry=None, alpha=1e-5,
                  quad_depth=3, stab="none", eps=0.0, f_lambda=1e-2, rho=1.0, c=1.0,
-                 E=1.0, nu=0.3, lo=None, hi=None, assemble=True):
+                 E=1.0, nu=0.3, lo=None, hi=None, assemble=True, workers=None):
         self.dim = dim
         self.n = np.array(n[:dim], dtype=int)
         self.p = p
@@ -79,9 +79,13 @@ class Discretization:
         self._number()
         self._reference_matrices()
         self.K_cut, self.M_cut_cons, self.M_cut_stab, self.ml_cut, self.scale_cut = {}, {}, {}, {}, {}
+        self._cut_km = {}
         if assemble:
+            if workers and workers > 1 and len(self.cut) > 1:
+                self._cut_km = _cut_integrals_in_pool(self, int(workers))
             for e in self.cut:
                 self._cut_matrices(e)
+            self._cut_km = {}
             self._assemble()
 
     # ---------------------------------------------------------------- geometry
@@ -157,12 +161,19 @@ class Discretization:
         self.M_full = np.diag(self.m_gll)
         self.lam_ref = element_lambda_max(self.K_ref, self.m_gll)
 
+    def _cut_integrals(self, e):
+        """K^e and the consistent M^e of a cut cell by the space-tree quadrature (alpha)."""
+        lo, hi = self.elem_box(e)
+        X, W, A = cut_cell_quadrature(self.geom, lo, hi, self.p, self.quad_depth, self.alpha)
+        return self._matrices(lo, hi, X, W, A)
+
     def _cut_matrices(self, e):
         """K^e, consistent M^e (alpha), stabilised M^e and the HRZ-lumped diagonal of a
         cut cell (stored in K_cut, M_cut_cons, M_cut_stab, ml_cut, scale_cut)."""
-        lo, hi = self.elem_box(e)
-        X, W, A = cut_cell_quadrature(self.geom, lo, hi, self.p, self.quad_depth, self.alpha)
-        K, M = self._matrices(lo, hi, X, W, A)
+        if e in self._cut_km:
+            K, M = self._cut_km[e]
+        else:
+            K, M = self._cut_integrals(e)
         self.K_cut[e] = K
         self.M_cut_cons[e] = M
         Ms = evs(M, self.M_full, self.eps, self.f_lambda) if self.stab == "evs" else M
@@ -436,6 +447,25 @@ class Discretization:
         for e in self.cut:
             mark[self.elem_dofs[e]] = True
         return np.nonzero(mark)[0]
+
+
+def _cut_integrals_of(args):
+    disc, cells = args
+    return {e: disc._cut_integrals(e) for e in cells}
+
+
+def _cut_integrals_in_pool(disc, workers):
+    """The cut cells' K^e, M^e (the same function per cell as the serial loop) on a pool of
+    spawned processes; only the work is split, every cell's arithmetic is unchanged."""
+    import multiprocessing as mp
+    cells = [int(e) for e in disc.cut]
+    n = max(1, min(workers, len(cells)))
+    chunks = [cells[i::n] for i in range(n)]
+    out = {}
+    with mp.get_context("spawn").Pool(n) as pool:
+        for res in pool.map(_cut_integrals_of, [(disc, c) for c in chunks]):
+            out.update(res)
+    return out
 
 
 def from_workload(w, **over):

@@ -44,9 +44,12 @@ def start_vector(n):
     return 1.0 + 0.5 * np.sin(np.arange(n, dtype=np.float64))
 
 
-def power_iteration(K, ML, max_iter=500, rtol=1e-10, mask=None):
-    """Returns (lambda, iterations).  ``mask`` restricts to a DOF subset (zero elsewhere)."""
+def power_iteration(K, ML, max_iter=500, rtol=1e-10, mask=None, threads=None):
+    """Returns (lambda, iterations).  ``mask`` restricts to a DOF subset (zero elsewhere);
+    ``threads`` splits the mat-vec into row blocks (bitwise the serial product)."""
+    from .integrators import RowBlockMatvec
     n = K.shape[0]
+    Kx = RowBlockMatvec(K, threads)
     s = 1.0 / np.sqrt(ML)
     w = start_vector(n)
     if mask is not None:
@@ -56,7 +59,7 @@ def power_iteration(K, ML, max_iter=500, rtol=1e-10, mask=None):
     lam = 0.0
     it = 0
     for it in range(1, max_iter + 1):
-        z = s * (K @ (s * w))
+        z = s * Kx(s * w)
         if mask is not None:
             z = np.where(mask, z, 0.0)
         lam = float(w @ z)
@@ -65,6 +68,7 @@ def power_iteration(K, ML, max_iter=500, rtol=1e-10, mask=None):
         if lam_old is not None and abs(lam - lam_old) <= rtol * abs(lam):
             break
         lam_old = lam
+    Kx.close()
     return lam, it
 
 

@@ -232,3 +232,23 @@ def test_consistent_mass_cdm_stability_limit():
             u, _ = OI.imex(sys_, 3000, u0=u0)
             nu = np.linalg.norm(u)
         assert (not np.isfinite(nu) or nu > 1e3 * np.linalg.norm(u0)) == grows
+
+
+def test_threaded_matvec_and_pooled_setup_are_bitwise_serial():
+    """The row-blocked threaded mat-vec and the cut-cell integrals on a process pool only
+    split the work: a CDM run and the assembled matrices equal the serial ones bitwise."""
+    from paper_2501_19013_gb300 import workloads as W
+    from oracle.discretization import from_workload
+    w = W.plate_holes_elastic(n=12, p=3, count=3, steps=40)
+    d1 = from_workload(w)
+    d2 = from_workload(w, workers=3)
+    assert (d1.K != d2.K).nnz == 0 and np.array_equal(d1.ML, d2.ML)
+    F = source_vector(d1, w.source)
+    rng = np.random.default_rng(4)
+    u0 = rng.standard_normal(d1.n_dof)
+    a = OI.cdm(d1.K, d1.ML, 1e-3, 30, u0=u0, F=F, f_e=w.f0)
+    b = OI.cdm(d1.K, d1.ML, 1e-3, 30, u0=u0, F=F, f_e=w.f0, threads=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    l1 = eigen.power_iteration(d1.K, d1.ML, max_iter=50)
+    l2 = eigen.power_iteration(d1.K, d1.ML, max_iter=50, threads=4)
+    assert l1 == l2
