@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from paper_2501_19013_gb300.metrics import observer_error, sample_rows
+from paper_2501_19013_gb300.metrics import observer_error, observer_errors, sample_rows
 
 
 def test_sample_rows_are_the_equidistant_instants():
@@ -41,3 +41,18 @@ def test_observer_error_components_and_zero_reference():
     assert observer_error(a, ref, 100, ncomp=2) == pytest.approx(want, rel=1e-12)
     with pytest.raises(ValueError):
         observer_error(a[:, :3], ref[:, :3], 100, ncomp=2)
+
+
+def test_observers_the_wave_has_not_reached_are_left_out():
+    """An observer whose reference series is 1e-12 of the others' (the precursor of a pulse
+    that has not arrived) is left out of the mean, and counted; at floor 0 it is kept and
+    its relative error (noise) dominates."""
+    t = np.linspace(0.0, 1.0, 201)
+    ref = np.stack([np.sin(9 * t), np.cos(4 * t), 1e-12 * np.sin(3 * t)], axis=1)
+    a = ref * np.array([1.0 + 1e-6, 1.0 - 2e-6, 1.0])
+    a[:, 2] += 1e-12            # relative noise of 1 on the unreached observer
+    r = observer_errors(a, ref, 100)
+    assert r["left_out"] == 1 and r["per_observer"][2] is None
+    assert r["mean"] == pytest.approx(1.5e-6, rel=1e-6)
+    assert observer_error(a, ref, 100) == r["mean"]
+    assert observer_error(a, ref, 100, floor=0.0) > 0.1
