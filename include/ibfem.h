@@ -377,6 +377,17 @@ int ibfem_batch_sync(ibfem_batch_t* b);
  * counter reached) and free the batch (NULL is accepted).  Always returns IBFEM_OK.       */
 int ibfem_batch_destroy(ibfem_batch_t* b);
 
+/* ---- failure detection ---------------------------------------------------------------- */
+
+/* Library runtime diagnostic (the paper has no counterpart): enqueues on the handle's stream
+ * one wait of the kind the tensor-core kernel uses for its MMA completions, on an mbarrier
+ * that nothing arrives on (no MMA or copy in flight), limited to `polls` try_wait calls.
+ * The wait runs out, records the timeout in the handle's device flag word and returns, so
+ * the next ibfem_sync / ibfem_sample returns IBFEM_ERR_TIMEOUT while the CUDA context stays
+ * usable; ibfem_set_initial / ibfem_set_state clear the record.  Asynchronous.
+ * Errors: ARG (polls outside [1, 2^24]), STATE (host-only handle), CUDA (launch). */
+int ibfem_check_bounded_wait(ibfem_t* h, int polls);
+
 /* ---- allocation-free operator ----------------------------------------------------- */
 
 /* y = K x on the node lattice, for callers that cannot allocate device memory: an
@@ -388,7 +399,9 @@ int ibfem_batch_destroy(ibfem_batch_t* b);
  * only scratch, the products K^e x_e of the cut cells, lives in a static device array of
  * 2^19 doubles (4 MiB) that every GPU loading the library holds until the process exits.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress,
- * with the device current); make that first call before any stream capture.  All calls
+ * with the device current) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point after cudaDeviceReset (or
+ * anything else that unloads the module), since the kept address would then be stale.  All calls
  * share the array and it keeps the last call's contents; every entry a call reads is
  * written by the same call first, so nothing needs clearing.  Calls whose kernels overlap
  * on the GPU (different streams, or different threads) race on the array: serialise them.

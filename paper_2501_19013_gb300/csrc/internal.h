@@ -146,6 +146,8 @@ cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int
 cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, int variant, const BatchMember* members,
                                const int* tile_start, int n_members, int total_tiles, BatchCtl* ctl,
                                cudaStream_t st);
+// One bounded mbarrier wait that runs out (nothing arrives): sets bit 1 of *flags.
+cudaError_t launch_bounded_wait_probe(int* flags, int polls, cudaStream_t st);
 bool op_tc_supported(int dim, int p, int ncomp);
 void op_tc_tiles(int dim, int p, int ncomp, int variant, int* tile);
 void op_tc_dims(int dim, int p, int ncomp, int* kp, int* np);

@@ -108,9 +108,11 @@ __device__ __forceinline__ uint16_t bf16_rn(float f) {
   return (uint16_t)(b >> 16);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase `parity` of an mbarrier: at most `polls` try_wait calls (each
+// may suspend the thread for a hardware-defined while); false when the phase never came.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int polls = 1 << 24) {
   uint32_t ok = 0;
-  for (int it = 0; it < (1 << 24) && !ok; ++it)
+  for (int it = 0; it < polls && !ok; ++it)
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
@@ -186,7 +188,27 @@ __device__ __forceinline__ void fp64_digits(double x, int em, int d[4]) {
   d[3] = neg ? -d3 : d3;
 }
 
+// Diagnostic of the bounded waits: one thread waits, with the poll limit given by the host,
+// on an mbarrier that nothing arrives on (no MMA or copy is in flight), exactly as the
+// operator kernel waits for its MMA completions; when the limit runs out it records the
+// timeout in the problem's flag word (bit 1), the same record the operator kernel leaves,
+// and returns.
+__global__ void bounded_wait_probe_kernel(int* flags, int polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if (!mbar_wait(smem_u32(&bar), 0u, polls)) atomicOr(flags, 2);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bounded_wait_probe(int* flags, int polls, cudaStream_t st) {
+  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(flags, polls);
+  return cudaGetLastError();
+}
 
 // Tile shapes (owned cells per axis; the halo adds one cell on the low side of each axis,
 // and the halo'd tile must fit the M = 128 rows of one MMA).  Variant 0 fills the MMA;

@@ -1215,6 +1215,16 @@ int ibfem_get_state(ibfem_t* h, double* u, double* u_prev) {
   IBFEM_CATCH
 }
 
+int ibfem_check_bounded_wait(ibfem_t* h, int polls) {
+  int rc = require_device(h);
+  if (rc) return rc;
+  if (polls < 1 || polls > (1 << 24)) return fail(IBFEM_ERR_ARG, "polls must be in [1, 2^24]");
+  IBFEM_TRY
+  check(launch_bounded_wait_probe(h->dev.flags, polls, h->stream), "bounded_wait_probe");
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
 int ibfem_set_state(ibfem_t* h, const double* u, const double* u_prev, int64_t step) {
   int rc = require_device(h);
   if (rc) return rc;

@@ -94,6 +94,7 @@ def lib():
         "ibfem_set_dt": (C.c_int, [vp, C.c_double]),
         "ibfem_step": (C.c_int, [vp, C.c_int64]),
         "ibfem_sync": (C.c_int, [vp]),
+        "ibfem_check_bounded_wait": (C.c_int, [vp, C.c_int]),
         "ibfem_step_timed": (C.c_int, [vp, C.c_int64, vp, C.c_size_t, DP, C.c_int, C.POINTER(C.c_int)]),
         "ibfem_kernel_name": (C.c_char_p, [vp, C.c_int]),
         "ibfem_sample": (C.c_int, [vp, C.c_int64, DP, C.POINTER(C.c_int64)]),
@@ -146,7 +147,8 @@ class Solver:
     def __init__(self, dim, n, p, *, lo=None, hi=None, physics="scalar", rho=1.0, c=1.0,
                  E=1.0, nu=0.3, alpha=1e-5, holes=None, voxels=None, rotated_box=None,
                  quad_depth=3, stab="none", eps=0.0, f_lambda=1e-2, scheme="cdm",
-                 precision="fp64", stream=None, device=0, host_only=False, torch_alloc=False):
+                 precision="fp64", stream=None, device=0, host_only=False, torch_alloc=False,
+                 allocator=None):
         L = lib()
         g = Grid()
         g.dim = dim
@@ -184,18 +186,27 @@ class Solver:
         o.stream = stream
         o.device = device
         o.host_only = 1 if host_only else 0
-        if torch_alloc:
+        if torch_alloc and allocator is None:
             import torch
             dev = device
 
+            def _talloc(nbytes):
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+
+            allocator = (_talloc, torch.cuda.caching_allocator_delete)
+        if allocator is not None:
+            # ``allocator`` = (alloc(nbytes) -> device address or None, free(address)): the
+            # library's dev_alloc / dev_free callbacks (a None or an exception is a failure)
+            a_fn, f_fn = allocator
+
             def _alloc(nbytes, ctx):
                 try:
-                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+                    return a_fn(int(nbytes))
                 except Exception:
                     return None
 
             def _free(ptr, ctx):
-                torch.cuda.caching_allocator_delete(ptr)
+                f_fn(ptr)
 
             self._alloc_cb = ALLOC_FN(_alloc)
             self._free_cb = FREE_FN(_free)
@@ -298,6 +309,10 @@ class Solver:
 
     def sync(self):
         _check(lib().ibfem_sync(self.h))
+
+    def check_bounded_wait(self, polls):
+        """Enqueue one bounded wait that runs out (``ibfem_check_bounded_wait``)."""
+        _check(lib().ibfem_check_bounded_wait(self.h, int(polls)))
 
     def sample(self, max_rows):
         nr = self.n_obs * self.ncomp
