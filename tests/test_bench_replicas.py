@@ -66,7 +66,38 @@ def test_accuracy_against_fp64_on_fake_runs():
     assert abs(results["exact"]["rel_l2"] - 3e-6) < 1e-12
     assert abs(results["exact"]["e_obs"]["e_100"] - 2e-6) < 1e-12
     assert abs(results["exact"]["e_obs"]["e_1000"] - 2e-6) < 1e-12
+    assert results["exact"]["e_obs"]["e_N"] == results["exact"]["e_obs"]["e_1000"]
+    assert results["exact"]["e_obs"]["observers_left_out"] == 0
+    assert len(results["exact"]["e_obs"]["e_1000_per_observer"]) == 3
     assert results["imex"]["rel_l2"] is None and results["imex"]["e_obs"] is None
     del results["fp64"]
     bench.accuracy_against_fp64(results)
     assert results["exact"]["rel_l2"] is None
+
+
+def test_qualification_needs_both_accuracy_measures():
+    """A variant counts toward time-to-accuracy only if its final-field rel-L2 and its
+    observer error e_N are both within 1e-4 of the FP64 path."""
+    import bench
+    ok = {"rel_l2": 2e-6, "e_obs": {"e_N": 3e-6}}
+    bad_obs = {"rel_l2": 2e-6, "e_obs": {"e_N": 0.5}}
+    bad_field = {"rel_l2": 2e-3, "e_obs": {"e_N": 1e-6}}
+    assert bench.qualifies(ok) and not bench.qualifies(bad_obs) and not bench.qualifies(bad_field)
+    assert not bench.qualifies({"rel_l2": None, "e_obs": None})
+    assert bench.qualifies({"rel_l2": 0.0, "e_obs": None})
+
+
+def test_algorithmic_bytes_follow_the_roofline_model():
+    """32 B per DOF + packed symmetric FP64 cut matrices + 4 B per cell; the plate benchmark
+    (1 873 378 DOFs, 1 281 distinct cut matrices of n_loc = 50, 256^2 cells) moves 73.3 MB."""
+    import bench
+
+    class Inf:
+        n_dof, n_loc, n_cut_matrices = 1873378, 50, 1281
+
+    class Wl:
+        dim, n = 2, (256, 256)
+
+    b = bench.algorithmic_bytes(Inf(), Wl())
+    assert b == 32 * 1873378 + 1281 * 50 * 51 * 4 + 4 * 65536
+    assert abs(b - 73.3e6) < 0.05e6
