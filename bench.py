@@ -329,6 +329,7 @@ MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 
 
 # arithmetic of each variant's element operator (the state and the update are FP64 in all)
 DTYPES = {"fp64": "f64",
+          "exact64": "f64-grade: bf16 8-bit slices (7 per operand), exact f32 accumulation, integer assembly, f64 state",
           "exact": "bf16 8-bit slices, exact f32 accumulation, f64 state",
           "bf16x3": "bf16x3, f32 accumulation, f64 state",
           "bf16": "bf16, f32 accumulation, f64 state"}

@@ -78,7 +78,11 @@ enum { IBFEM_FP64 = 0,          /* FP64 contractions on the CUDA cores          
                                    K_ref (BF16) accumulated exactly per level (10 MMA chains),
                                    level 0 summed error-free: about 32 significant bits      */
        IBFEM_BF16X3_TC = 2,     /* tcgen05 kind::f16, BF16 hi/lo splits, 3 passes, FP32 acc. */
-       IBFEM_BF16_TC = 3        /* tcgen05 kind::f16, one BF16 pass, FP32 accumulation      */ };
+       IBFEM_BF16_TC = 3,       /* tcgen05 kind::f16, one BF16 pass, FP32 accumulation      */
+       IBFEM_EXACT64_TC = 4     /* FP64-grade: tcgen05 kind::f16, seven balanced 8-bit digit
+                                   slices of u and K_ref (one exponent for K_ref), all levels
+                                   s + t <= 6 (28 MMA chains) exact, integer node sums, K u
+                                   rounded once in FP64; cut cells by the FP64 cut kernel    */ };
 enum { IBFEM_SRC_NONE = 0,
        IBFEM_SRC_POINT = 1,          /* params: x, y[, z] [, dir_x, dir_y] (elastic)   */
        IBFEM_SRC_EDGE_TRACTION = 2,  /* params: y0, y1, t_x[, t_y]; edge x = lo_x (2D) */

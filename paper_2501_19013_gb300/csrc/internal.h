@@ -48,6 +48,7 @@ struct DevProblem {
   int tc_tiles[3];          // tile grid of the tensor-core kernel
   const uint16_t* tc_bimg;  // K_ref as UMMA B operand: four BF16 slices (digits or hi/lo)
   const int* tc_frow;       // exact scheme: unbiased exponent F_i of each K_ref row
+  int tc_gexp;              // FP64-grade scheme: unbiased exponent G of K_ref's largest entry
   const int32_t* tc_order;  // tensor-core tiles in processing order (costliest first), or null
   const float* minv32;      // dt^2 / M_L as two FP32 slices: hi[n_lat_dof] then lo[n_lat_dof]
   const int32_t* tsrc_ptr;  // source CSR over the tensor-core tile grid
@@ -146,6 +147,11 @@ cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int
 cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, int variant, const BatchMember* members,
                                const int* tile_start, int n_members, int total_tiles, BatchCtl* ctl,
                                cudaStream_t st);
+// Launchers (kernels_tc64.cu): the FP64-grade tensor-core operator (CDM, start-up or apply
+// mode); pb.Ycut must hold this input's cut-cell products (launch_cut_apply_fp64 first).
+// Its tile shape is variant op_tc64_variant(dim) of op_tc_tiles.
+cudaError_t launch_op_tc64(const DevProblem& pb, const double* u, double* out, int mode, cudaStream_t st);
+int op_tc64_variant(int dim);
 // One bounded mbarrier wait that runs out (nothing arrives): sets bit 1 of *flags.
 cudaError_t launch_bounded_wait_probe(int* flags, int polls, cudaStream_t st);
 bool op_tc_supported(int dim, int p, int ncomp);

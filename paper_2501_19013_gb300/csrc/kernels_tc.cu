@@ -34,124 +34,13 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace ibfem {
 
+using namespace tc;
+
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// FP32 -> FP64 exactly by bit manipulation with an extra power-of-two scale 2^sh
-// (integer pipe only; zero and subnormal inputs give zero).
-__device__ __forceinline__ double f32_to_f64_scaled(float f, int sh) {
-  uint32_t b = __float_as_uint(f);
-  int e = (int)((b >> 23) & 0xffu);
-  if (e == 0) return 0.0;
-  uint32_t sign = b & 0x80000000u, m = b & 0x7fffffu;
-  int e64 = e + 896 + sh;
-  if (e64 <= 0) return 0.0;                                   // below FP64 normals: negligible
-  if (e64 >= 2047) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
-  uint32_t hi = sign | ((uint32_t)e64 << 20) | (m >> 3);
-  uint32_t lo = m << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-// f * 2^sh in FP32 by exponent arithmetic (flush to zero on underflow)
-__device__ __forceinline__ float f32_scale(float f, int sh) {
-  uint32_t b = __float_as_uint(f);
-  int e = (int)((b >> 23) & 0xffu);
-  if (e == 0) return 0.f;
-  int e2 = e + sh;
-  if (e2 <= 0) return 0.f;
-  if (e2 >= 255) return __uint_as_float((b & 0x80000000u) | 0x7f800000u);
-  return __uint_as_float((b & 0x807fffffu) | ((uint32_t)e2 << 23));
-}
-
-// FP64 -> FP32 rounding to nearest by bit manipulation (ties away from zero).
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-  uint32_t sign = hi & 0x80000000u;
-  int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
-  uint32_t r = ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  r += (lo >> 28) & 1u;  // carry may bump the exponent: still correct
-  return __uint_as_float(sign | r);
-}
-
-__device__ __forceinline__ double ricker_tc(double t, double f_e) {
-  const double pi = 3.141592653589793238462643383279502884;
-  double ts = 2.0 * sqrt(6.0) / (pi * f_e);
-  double q = pi * f_e * (t - ts);
-  return (1.0 - 2.0 * q * q) * exp(-q * q);
-}
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0; no swizzle
-  return d;
-}
-
-__device__ __forceinline__ uint16_t bf16_of_small_int(int v) {
-  // |v| <= 256 has at most 8 significant bits: the upper half of its FP32 pattern is exact
-  return (uint16_t)(__float_as_uint((float)v) >> 16);
-}
-
-__device__ __forceinline__ uint16_t bf16_rn(float f) {
-  uint32_t b = __float_as_uint(f);
-  b += 0x7fffu + ((b >> 16) & 1u);  // round to nearest even (finite inputs)
-  return (uint16_t)(b >> 16);
-}
-
-// Bounded wait for the phase `parity` of an mbarrier: at most `polls` try_wait calls (each
-// may suspend the thread for a hardware-defined while); false when the phase never came.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int polls = 1 << 24) {
-  uint32_t ok = 0;
-  for (int it = 0; it < polls && !ok; ++it)
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-// error-free transformations of double-FP32 arithmetic
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-
-// Asynchronous copy global -> shared of 8 or 16 bytes; src_bytes = 0 writes zeros.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
-               "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
 
 // Balanced 8-bit digits of round(|x| 2^(31 - E)) for an FP64 x whose biased exponent is at
 // most em (the row's largest), sign applied to every digit; 32-bit integer operations only.
@@ -210,18 +99,6 @@ cudaError_t launch_bounded_wait_probe(int* flags, int polls, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Tile shapes (owned cells per axis; the halo adds one cell on the low side of each axis,
-// and the halo'd tile must fit the M = 128 rows of one MMA).  Variant 0 fills the MMA;
-// variant 1 is a smaller tile (more tiles for small problems, less shared memory in 3D);
-// the autotuner picks between them per problem.
-__host__ __device__ constexpr int tc_tile_x(int dim, int nl, int v) {
-  return dim == 3 ? (v ? 3 : 4) : (nl >= 32 ? (v ? 5 : 8) : (v ? 7 : 15));
-}
-__host__ __device__ constexpr int tc_tile_y(int dim, int nl, int v) {
-  return dim == 3 ? (v ? 3 : 4) : (nl >= 32 ? (v ? 5 : 8) : 7);
-}
-__host__ __device__ constexpr int tc_tile_z(int dim, int v) { return dim == 3 ? (v ? 3 : 4) : 1; }
-
 template <int DIM, int P, int NC, int TILE>
 struct TcCfg {
   static constexpr int NN1 = P + 1;
@@ -251,7 +128,8 @@ struct TcCfg {
   static constexpr size_t PATCH_BYTES = (8 * (size_t)PATCH + 15) / 16 * 16;  // one patch buffer
   static constexpr size_t OFF_E = OFF_PATCH + 2 * PATCH_BYTES;              // int E[128]
   static constexpr size_t OFF_F = OFF_E + 4 * (4 + 128 + 8);                 // int F[NP]
-  static constexpr size_t OFF_OFF = OFF_F + 4 * (size_t)NP;                  // int off[KP]
+  static constexpr size_t OFF_SC = OFF_F + 4 * (size_t)NP;                   // float scale[NP]
+  static constexpr size_t OFF_OFF = OFF_SC + 4 * (size_t)NP;                 // int off[KP]
   static constexpr size_t OFF_XS = (OFF_OFF + 4 * (size_t)KP + 15) / 16 * 16;  // 8 warps x 2 x NL floats
   static constexpr size_t OFF_BAR = (OFF_XS + 4 * 2 * 8 * (size_t)NL + 15) / 16 * 16;
   static constexpr size_t SMEM = OFF_BAR + 64;
@@ -262,11 +140,6 @@ struct TcCfg {
   static_assert(NE <= 128, "halo'd tile must fit one M = 128 MMA");
   static_assert(KP % 8 == 0 && (KP / 8) <= 32, "K layout");
 };
-
-template <int KP>
-__host__ __device__ __forceinline__ int bf16_core_offset(int row, int k) {
-  return (row >> 3) * (KP / 8) * 64 + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
-}
 
 // scheme: 0 exact, 1 bf16x3, 2 bf16.  Persistent: each CTA loads the K_ref digits once and
 // takes tiles from a global counter until none are left.
@@ -295,6 +168,7 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
   int pcur = 0;
   int* Eb = reinterpret_cast<int*>(smem + C::OFF_E);          // Eb[0]: tile exponent; Eb[1..]: lists
   int* Fr = reinterpret_cast<int*>(smem + C::OFF_F);
+  float* scl = reinterpret_cast<float*>(smem + C::OFF_SC);   // per tile: 2^(E + F_i - 1037)
   int* off = reinterpret_cast<int*>(smem + C::OFF_OFF);
   float* xs = reinterpret_cast<float*>(smem + C::OFF_XS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // 0: B copy, 1: MMA phase 1, 2: phase 2
@@ -542,6 +416,12 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
       em = wmax[0];
 #pragma unroll
       for (int w = 1; w < 8; ++w) em = max(em, wmax[w]);
+      // the drain's scale of output row i: 2^(E + F_i - 1037), zero below the FP32 normals
+      // (read after the barrier that ends the digit conversion)
+      for (int i = tid; i < NP; i += blockDim.x) {
+        const int sh = em - 1023 - 14 + Fr[i];
+        scl[i] = sh < -126 ? 0.f : __int_as_float((min(sh, 127) + 127) << 23);
+      }
     }
     for (int i = tid; i < NV; i += blockDim.x) {
       double x = pf[i];
@@ -549,8 +429,8 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
       if (SCHEME == 0) {
         int dg[4];
         fp64_digits(x, em, dg);
-        lo16 = bf16_of_small_int(dg[0]) | ((uint32_t)bf16_of_small_int(dg[1]) << 16);
-        hi16 = bf16_of_small_int(dg[2]) | ((uint32_t)bf16_of_small_int(dg[3]) << 16);
+        lo16 = bf16x2_of_small_ints(dg[0], dg[1]);
+        hi16 = bf16x2_of_small_ints(dg[2], dg[3]);
       } else {
         float xf = f64_to_f32_rn(x);
         uint16_t h = bf16_rn(xf);
@@ -674,7 +554,6 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
       // quarter w % 4 and split the column blocks.
       const int m = (warp & 3) * 32 + lane;
       const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-      const int ebase = em - 1023 - 14;
 #pragma unroll 1
       for (int c0 = (warp >> 2) * 16; c0 < NP; c0 += 32) {
         uint32_t r[4][16];
@@ -689,14 +568,24 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
               : "r"(addr));
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float scq[16];
+        if (SCHEME == 0) {
+#pragma unroll
+          for (int q = 0; q < 16; q += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(scl + c0 + q);
+            scq[q] = v.x;
+            scq[q + 1] = v.y;
+            scq[q + 2] = v.z;
+            scq[q + 3] = v.w;
+          }
+        }
         if (m < C::NE) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             int i = c0 + q;
             if (i < NL) {
               if (SCHEME == 0) {
-                const int sh = ebase + Fr[i];
-                const float sc = sh < -126 ? 0.f : __int_as_float((min(sh, 127) + 127) << 23);
+                const float sc = scq[q];
                 float lo = fmaf(__uint_as_float(r[1][q]), 0.00390625f,
                                 fmaf(__uint_as_float(r[2][q]), 1.52587890625e-05f,
                                      __uint_as_float(r[3][q]) * 5.9604644775390625e-08f));
@@ -785,71 +674,122 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
       __syncwarp();
     }
     __syncthreads();
-    // ---- node-centric assembly and the FP64 update (owned nodes, no runtime division)
+    // ---- node-centric assembly and the FP64 update.  Each owned cell owns the nodes whose
+    // local indices all lie below P (its low corner block), so the cells around an owned
+    // node sit at fixed offsets of the halo'd tile and of their output rows; the nodes on
+    // the domain's high faces (local index P in the last cell) follow in a second pass.
+    // The cells of a node are summed in the order (z, y, x) of their offsets, lower first.
     const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
-    const int nox = (X1 - X0) * P + (X1 == pb.n[0] ? 1 : 0);
-    const int noy = (Y1 - Y0) * P + (Y1 == pb.n[1] ? 1 : 0);
-    const int noz = DIM == 3 ? (Z1 - Z0) * P + (Z1 == pb.n[2] ? 1 : 0) : 1;
-    constexpr int WX = C::TX * P + 1, WY = C::TY * P + 1, WZ = DIM == 3 ? C::TZ * P + 1 : 1;
     int src_lo = 0, src_hi = 0;
     if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) {
       src_lo = pb.tsrc_ptr[tile];
       src_hi = pb.tsrc_ptr[tile + 1];
     }
-    constexpr int TOTAL = WX * WY * WZ * NC;
-    // every global load of a thread's items is issued before any of them is used (one
-    // memory round trip per tile instead of one per few items)
-    constexpr int NB = (TOTAL + 255) / 256 < 5 ? (TOTAL + 255) / 256 : 5;
-    auto decode = [&](int i, int& comp, int& lx, int& ly, int& lz) {
-      comp = i % NC;
-      const int node = i / NC;
-      lx = node % WX;
-      ly = (node / WX) % WY;
-      lz = node / (WX * WY);
+    // the update of one owned DOF from its sum -K u = -(sh + (se + lo))
+    auto update = [&](int64_t dof, float sh, float se, float lo, double uval, double upv, float mh, float ml) {
+      if (mode == kModeApply) {
+        out[dof] = f32_to_f64_scaled(sh, 0) + f32_to_f64_scaled(se + lo, 0);
+        return;
+      }
+      if (!(mh > 0.f)) return;
+      const float r = -(sh + (se + lo));   // -K u rounded once to FP32 (the load follows below)
+      const float d32 = fmaf(mh, r, ml * r);
+      if (!isfinite(d32)) bad = true;
+      const double delta = f32_to_f64_scaled(d32, 0);
+      if (mode == kModeCDM)
+        out[dof] = fma(2.0, uval, -upv) + delta;
+      else
+        out[dof] = uval - pb.dt * upv + 0.5 * delta;
     };
-    for (int base = tid; base < TOTAL; base += NB * 256) {
-      double upv[NB], ukv[NB];
-      float mhv[NB], mlv[NB];
+    {
+      constexpr int PD = DIM == 3 ? P * P * P : P * P;
+      constexpr int OWNC = PD * NC;                                 // DOFs a cell owns
+      constexpr int NCELL = C::TX * C::TY * C::TZ;
+      constexpr int TOT = OWNC * NCELL;
+      constexpr int NB = (TOT + 255) / 256 < 4 ? (TOT + 255) / 256 : 4;
+      // offsets (in float2 entries of yb) of the lower neighbours' rows of the same node
+      constexpr int DX = NL - P * NC, DY = EX * NL - P * NN1 * NC, DZ = EX * EY * NL - P * NN1 * NN1 * NC;
+      const int tx = X1 - X0, ty = Y1 - Y0, tz = DIM == 3 ? Z1 - Z0 : 1;
+      for (int base = tid; base < TOT; base += NB * 256) {
+        double upv[NB], ukv[NB];
+        float mhv[NB], mlv[NB];
+        int64_t dofv[NB];
+        int yix[NB], key[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int i = base + b * 256;
-        int comp, lx, ly, lz;
-        decode(i, comp, lx, ly, lz);
-        const bool act = i < TOTAL && lx < nox && ly < noy && lz < noz;
-        const int64_t dof = (((int64_t)(oz0 + lz) * pb.lat[1] + (oy0 + ly)) * pb.lat[0] + (ox0 + lx)) * NC + comp;
-        upv[b] = 0.0;
-        ukv[b] = 0.0;
-        mhv[b] = 0.f;
-        mlv[b] = 0.f;
-        if (act && mode != kModeApply) {
-          mhv[b] = __ldg(pb.minv32 + dof);
-          mlv[b] = __ldg(pb.minv32 + pb.n_lat_dof + dof);
-          upv[b] = out[dof];
-          ukv[b] = pf[(((DIM == 3 ? lz + P : 0) * PY + (ly + P)) * PX + (lx + P)) * NC + comp];
+        for (int b = 0; b < NB; ++b) {
+          const int i = base + b * 256;
+          const int q = i % OWNC, cell = i / OWNC;
+          const int comp = q % NC, nd = q / NC;
+          const int a = nd % P, bb = (nd / P) % P, cc = DIM == 3 ? nd / (P * P) : 0;
+          const int ox = cell % C::TX, oy = (cell / C::TX) % C::TY, oz = DIM == 3 ? cell / (C::TX * C::TY) : 0;
+          const bool act = i < TOT && ox < tx && oy < ty && oz < tz;
+          const int lx = ox * P + a, ly = oy * P + bb, lz = oz * P + cc;
+          const int64_t dof = (((int64_t)(oz0 + lz) * pb.lat[1] + (oy0 + ly)) * pb.lat[0] + (ox0 + lx)) * NC + comp;
+          // own cell (ox + 1, oy + 1[, oz + 1]) of the halo'd tile and the node's row in it
+          const int m = ((DIM == 3 ? oz + 1 : 0) * EY + (oy + 1)) * EX + (ox + 1);
+          const int row = (((DIM == 3 ? cc * NN1 : 0) + bb) * NN1 + a) * NC + comp;
+          dofv[b] = act ? dof : -1;
+          yix[b] = m * NL + row;
+          key[b] = (a == 0 ? 1 : 0) | (bb == 0 ? 2 : 0) | (DIM == 3 && cc == 0 ? 4 : 0);
+          upv[b] = 0.0;
+          ukv[b] = 0.0;
+          mhv[b] = 0.f;
+          mlv[b] = 0.f;
+          if (act && mode != kModeApply) {
+            mhv[b] = __ldg(pb.minv32 + dof);
+            mlv[b] = __ldg(pb.minv32 + pb.n_lat_dof + dof);
+            upv[b] = out[dof];
+            ukv[b] = pf[(((DIM == 3 ? lz + P : 0) * PY + (ly + P)) * PX + (lx + P)) * NC + comp];
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          if (dofv[b] < 0) continue;
+          // level-0 parts summed error-free in FP32 (sh + se is their exact sum)
+          float sh = 0.f, se = 0.f, lo = 0.f;
+#pragma unroll
+          for (int jz = 0; jz < (DIM == 3 ? 2 : 1); ++jz)
+#pragma unroll
+            for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+              for (int jx = 0; jx < 2; ++jx) {
+                const bool val = (jx || (key[b] & 1)) && (jy || (key[b] & 2)) && (DIM == 2 || jz || (key[b] & 4));
+                if (val) {
+                  const int off_n = (jx ? 0 : DX) + (jy ? 0 : DY) + (DIM == 3 && !jz ? DZ : 0);
+                  const float2 y = yb[yix[b] - off_n];
+                  float t1, t2;
+                  two_sum(sh, y.x, t1, t2);
+                  sh = t1;
+                  se += t2;
+                  lo += y.y;
+                }
+              }
+          update(dofv[b], sh, se, lo, ukv[b], upv[b], mhv[b], mlv[b]);
         }
       }
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int i = base + b * 256;
-        int comp, lx, ly, lz;
-        decode(i, comp, lx, ly, lz);
-        if (!(i < TOTAL && lx < nox && ly < noy && lz < noz)) continue;
+    }
+    // nodes on the domain's high faces (their cell's local index P): generic search of the
+    // (up to 2^DIM) cells that hold them, in the same order
+    if (X1 == pb.n[0] || Y1 == pb.n[1] || (DIM == 3 && Z1 == pb.n[2])) {
+      const int ex_ = (X1 - X0) * P, ey_ = (Y1 - Y0) * P, ez_ = DIM == 3 ? (Z1 - Z0) * P : 0;
+      const int nox = ex_ + (X1 == pb.n[0] ? 1 : 0);
+      const int noy = ey_ + (Y1 == pb.n[1] ? 1 : 0);
+      const int noz = DIM == 3 ? ez_ + (Z1 == pb.n[2] ? 1 : 0) : 1;
+      const int total = nox * noy * noz * NC;
+      for (int i = tid; i < total; i += blockDim.x) {
+        const int comp = i % NC, node = i / NC;
+        const int lx = node % nox, ly = (node / nox) % noy, lz = node / (nox * noy);
+        if (!(lx == ex_ || ly == ey_ || (DIM == 3 && lz == ez_))) continue;   // first pass
         const int64_t dof = (((int64_t)(oz0 + lz) * pb.lat[1] + (oy0 + ly)) * pb.lat[0] + (ox0 + lx)) * NC + comp;
-        // the (up to 2^DIM) cells of the halo'd tile that hold this node, in a fixed order;
-        // level-0 parts summed error-free in FP32 (s + e is their exact sum)
         const int px = lx + P, py = ly + P, pz = DIM == 3 ? lz + P : 0;
         const int cx = px / P, cy = py / P, cz = DIM == 3 ? pz / P : 0;
         const bool bx = px - cx * P == 0, by = py - cy * P == 0, bz = DIM == 3 && pz - cz * P == 0;
         float sh = 0.f, se = 0.f, lo = 0.f;
-#pragma unroll
         for (int jz = 0; jz < (DIM == 3 ? 2 : 1); ++jz)
-#pragma unroll
           for (int jy = 0; jy < 2; ++jy)
-#pragma unroll
             for (int jx = 0; jx < 2; ++jx) {
               const int ecx = cx - 1 + jx, ecy = cy - 1 + jy, ecz = DIM == 3 ? cz - 1 + jz : 0;
-              const bool val = (jx ? cx < EX : bx) && (jy ? cy < EY : by) &&
-                               (DIM == 2 || (jz ? cz < C::EZ : bz));
+              const bool val = (jx ? cx < EX : bx) && (jy ? cy < EY : by) && (DIM == 2 || (jz ? cz < C::EZ : bz));
               if (val) {
                 const int m = (ecz * EY + ecy) * EX + ecx;
                 const int row = (((DIM == 3 ? (pz - ecz * P) * NN1 : 0) + (py - ecy * P)) * NN1 + (px - ecx * P)) * NC + comp;
@@ -861,20 +801,15 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
                 lo += y.y;
               }
             }
-        if (mode == kModeApply) {
-          out[dof] = f32_to_f64_scaled(sh, 0) + f32_to_f64_scaled(se + lo, 0);
-          continue;
+        float mh = 0.f, ml = 0.f;
+        double upv = 0.0, uval = 0.0;
+        if (mode != kModeApply) {
+          mh = __ldg(pb.minv32 + dof);
+          ml = __ldg(pb.minv32 + pb.n_lat_dof + dof);
+          upv = out[dof];
+          uval = pf[(((DIM == 3 ? lz + P : 0) * PY + (ly + P)) * PX + (lx + P)) * NC + comp];
         }
-        if (!(mhv[b] > 0.f)) continue;
-        const float r = -(sh + (se + lo));   // -K u rounded once to FP32 (the load follows below)
-        const float d32 = fmaf(mhv[b], r, mlv[b] * r);
-        if (!isfinite(d32)) bad = true;
-        const double delta = f32_to_f64_scaled(d32, 0);
-        const double uval = ukv[b];
-        if (mode == kModeCDM)
-          out[dof] = fma(2.0, uval, -upv[b]) + delta;
-        else
-          out[dof] = uval - pb.dt * upv[b] + 0.5 * delta;
+        update(dof, sh, se, lo, uval, upv, mh, ml);
       }
     }
     // the load F_k of this tile's DOFs (each DOF once per tile), added after the update in

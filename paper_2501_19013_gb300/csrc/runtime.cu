@@ -189,7 +189,8 @@ void Handle::build_device() {
     int kp = 0, np = 0;
     op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
     const size_t slice = (size_t)np * kp;
-    std::vector<uint16_t> img(4 * slice, 0);
+    const bool fp64grade = tc_scheme() == 3;
+    std::vector<uint16_t> img((fp64grade ? 7 : 4) * slice, 0);
     std::vector<int> frow(np, 0);
     auto bf16 = [](float f) {
       uint32_t b;
@@ -203,7 +204,36 @@ void Handle::build_device() {
       std::memcpy(&f, &b, 4);
       return f;
     };
-    for (int i = 0; i < s.n_loc; ++i) {
+    // FP64-grade scheme: one exponent G for the whole matrix (max |K| < 2^(G + 1)) and seven
+    // balanced 8-bit digits of round(|K_ij| 2^(54 - G)) < 2^55 (|digit| <= 128)
+    int G = 0;
+    if (fp64grade) {
+      double amax = 0.0;
+      for (double v : s.Kref) amax = std::max(amax, std::fabs(v));
+      if (amax > 0.0) {
+        G = (int)std::floor(std::log2(amax));
+        if (std::ldexp(1.0, G + 1) <= amax) ++G;
+        if (std::ldexp(1.0, G) > amax) --G;
+      }
+      for (int i = 0; i < s.n_loc; ++i)
+        for (int j = 0; j < s.n_loc; ++j) {
+          const double v = s.Kref[(size_t)i * s.n_loc + j];
+          unsigned long long W = (unsigned long long)std::llround(std::ldexp(std::fabs(v), 54 - G));
+          long long c[7];
+          int carry = 0;
+          for (int b = 0; b < 7; ++b) {   // byte b of W is digit 6 - b
+            int t = (int)((W >> (8 * b)) & 0xffu) + carry;
+            if (b < 6) {
+              carry = t >= 128 ? 1 : 0;
+              t -= carry << 8;
+            }
+            c[6 - b] = v < 0 ? -t : t;
+          }
+          const int o = op_tc_core_offset(kp, i, j);
+          for (int t = 0; t < 7; ++t) img[t * slice + o] = bf16((float)c[t]);
+        }
+    }
+    for (int i = 0; i < s.n_loc && !fp64grade; ++i) {
       double amax = 0.0;
       for (int j = 0; j < s.n_loc; ++j) amax = std::max(amax, std::fabs(s.Kref[(size_t)i * s.n_loc + j]));
       int F = 0;
@@ -234,30 +264,37 @@ void Handle::build_device() {
     to_shared = true;
     pb.tc_bimg = upload(img);
     pb.tc_frow = upload(frow);
+    pb.tc_gexp = G;
     tc_img_host = img;
     tc_frow_host = frow;
-    // cut matrices as interleaved (hi, lo) FP32 pairs: one 8-byte load per entry
-    std::vector<float> k32(2 * (size_t)s.n_cut_mat * s.n_loc * s.n_loc);
-    const size_t nl2 = (size_t)s.n_loc * s.n_loc;
-    for (int64_t c = 0; c < s.n_cut_mat; ++c)
-      for (size_t q = 0; q < nl2; ++q) {
-        double v = s.Kcut[c * nl2 + q];
-        float h = (float)v;
-        k32[2 * (c * nl2 + q)] = h;
-        k32[2 * (c * nl2 + q) + 1] = (float)(v - (double)h);
-      }
-    pb.Kcut32 = upload(k32);
-    to_shared = false;
-    std::vector<float> m32(2 * (size_t)s.n_lat_dof, 0.f);
-    for (int64_t i = 0; i < s.n_lat_dof; ++i)
-      if (s.ML[i] > 0) {
-        double v = 1.0 / s.ML[i];
-        float h = (float)v;
-        m32[i] = h;
-        m32[s.n_lat_dof + i] = (float)(v - (double)h);
-      }
-    d_minv32 = upload(m32);
-    pb.minv32 = d_minv32;
+    if (fp64grade) {
+      // the FP64 cut-cell kernel supplies the cut products; dt^2 / M_L is read in FP64
+      to_shared = false;
+      tc_variant = op_tc64_variant(s.dim);
+    } else {
+      // cut matrices as interleaved (hi, lo) FP32 pairs: one 8-byte load per entry
+      std::vector<float> k32(2 * (size_t)s.n_cut_mat * s.n_loc * s.n_loc);
+      const size_t nl2 = (size_t)s.n_loc * s.n_loc;
+      for (int64_t c = 0; c < s.n_cut_mat; ++c)
+        for (size_t q = 0; q < nl2; ++q) {
+          double v = s.Kcut[c * nl2 + q];
+          float h = (float)v;
+          k32[2 * (c * nl2 + q)] = h;
+          k32[2 * (c * nl2 + q) + 1] = (float)(v - (double)h);
+        }
+      pb.Kcut32 = upload(k32);
+      to_shared = false;
+      std::vector<float> m32(2 * (size_t)s.n_lat_dof, 0.f);
+      for (int64_t i = 0; i < s.n_lat_dof; ++i)
+        if (s.ML[i] > 0) {
+          double v = 1.0 / s.ML[i];
+          float h = (float)v;
+          m32[i] = h;
+          m32[s.n_lat_dof + i] = (float)(v - (double)h);
+        }
+      d_minv32 = upload(m32);
+      pb.minv32 = d_minv32;
+    }
     build_tc_tiles();
   }
   scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
@@ -309,8 +346,9 @@ void Handle::build_clone(const Handle& src) {
     check(cudaMemcpyAsync(d_minv32, src.d_minv32, 2 * s.n_lat_dof * sizeof(float), cudaMemcpyDeviceToDevice,
                           stream), "minv32");
     pb.minv32 = d_minv32;
-    build_tc_tiles();   // the source's tile order may be its own array (a later tile variant)
   }
+  if (opt.precision != IBFEM_FP64)
+    build_tc_tiles();   // the source's tile order may be its own array (a later tile variant)
   scalars = static_cast<double*>(dalloc(8 * sizeof(double)));
   lam_hist = static_cast<double*>(dalloc(kPowerChunk * sizeof(double)));
   scratch = static_cast<double*>(dalloc(s.n_lat_dof * sizeof(double)));
@@ -411,13 +449,13 @@ size_t Handle::planned_device_bytes() const {
   if (opt.precision != IBFEM_FP64) {
     int kp = 0, np = 0;
     op_tc_dims(s.dim, s.p, s.ncomp, &kp, &np);
-    b += 4 * (size_t)kp * np * 2 + arr(np, 4);            // K_ref image, row exponents
+    b += (tc_scheme() == 3 ? 7 : 4) * (size_t)kp * np * 2 + arr(np, 4);   // K_ref image, row exponents
     int tt[3] = {1, 1, 1};
-    op_tc_tiles(s.dim, s.p, s.ncomp, tc_variant, tt);
+    op_tc_tiles(s.dim, s.p, s.ncomp, tc_scheme() == 3 ? op_tc64_variant(s.dim) : tc_variant, tt);
     int64_t ntc = 1;
     for (int k = 0; k < s.dim; ++k) ntc *= (s.n[k] + tt[k] - 1) / tt[k];
     b += arr(ntc, 4);                                     // tile order
-    b += arr(2 * nmat * nl * nl, 4) + arr(2 * nlat, 4);   // Kcut32, minv32
+    if (tc_scheme() != 3) b += arr(2 * nmat * nl * nl, 4) + arr(2 * nlat, 4);   // Kcut32, minv32
   }
   b += 64 + kPowerChunk * 8 + arr(nlat, 8);               // scalars, lam_hist, scratch
   return b;
@@ -537,6 +575,22 @@ void Handle::timed_collect() {
 
 // One CDM step with u = U[cur], out = U[1 - cur] (in place over u^{k-1}).
 void Handle::enqueue_step(int cur) {
+  if (opt.precision == IBFEM_EXACT64_TC) {
+    // FP64-grade tensor-core step: the FP64 cut-cell products (and the observers), then the
+    // fused tensor-core operator and update
+    OpInput x{U[cur], nullptr, nullptr};
+    slot_name[1] = "cut_apply_fp64";
+    slot_name[2] = "op_tc_exact64_fused_cdm";
+    if (timing) step_first_ev.push_back(ev_used);
+    timed_begin(1);
+    check(launch_cut_apply_fp64(dev, x, true, stream), "cut_apply");
+    timed_end();
+    timed_begin(2);
+    check(launch_op_tc64(dev, U[cur], U[1 - cur], kModeCDM, stream), "op_tc64");
+    timed_end();
+    if (timing) step_last_ev.push_back(ev_used - 1);
+    return;
+  }
   if (opt.precision != IBFEM_FP64) {
     slot_name[1] = tc_scheme() == 0 ? "op_tc_exact_fused_cdm" : (tc_scheme() == 1 ? "op_tc_bf16x3_fused_cdm" : "op_tc_bf16_fused_cdm");
     if (timing) step_first_ev.push_back(ev_used);
@@ -703,7 +757,7 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
     throw std::invalid_argument("IMEX and the consistent-mass CDM run in FP64 (precision must be IBFEM_FP64)");
   in.need_consistent_mass = o.scheme != IBFEM_CDM;
   if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
-      o.precision != IBFEM_BF16_TC)
+      o.precision != IBFEM_BF16_TC && o.precision != IBFEM_EXACT64_TC)
     throw std::invalid_argument("unknown precision");
   if (!(o.rho > 0)) throw std::invalid_argument("rho must be > 0");
   if (stab) {
@@ -1256,7 +1310,10 @@ int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
   h->to_lattice(x, lx);
   check(cudaMemcpyAsync(h->W, lx.data(), lx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream), "x");
   OpInput in{h->W, nullptr, nullptr};
-  if (h->opt.precision != IBFEM_FP64) {
+  if (h->opt.precision == IBFEM_EXACT64_TC) {
+    check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
+    check(launch_op_tc64(h->dev, h->W, h->scratch, kModeApply, h->stream), "apply_tc64");
+  } else if (h->opt.precision != IBFEM_FP64) {
     check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_scheme(), h->tc_variant, h->stream), "apply_tc");
   } else {
     check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
@@ -1273,6 +1330,8 @@ int ibfem_set_tile_variant(ibfem_t* h, int variant) {
   int rc = require_device(h);
   if (rc) return rc;
   if (variant != 0 && variant != 1) return fail(IBFEM_ERR_ARG, "tile variant must be 0 or 1");
+  if (h->opt.precision == IBFEM_EXACT64_TC)
+    return variant == h->tc_variant ? IBFEM_OK : fail(IBFEM_ERR_ARG, "the FP64-grade tensor-core path has one tile shape");
   if (variant == 1 && h->tc_scheme() != 0)
     return fail(IBFEM_ERR_ARG, "the small tile exists for the exact tensor-core path (IBFEM_EXACT_TC)");
   if (h->opt.precision == IBFEM_FP64) return variant == 0 ? IBFEM_OK : fail(IBFEM_ERR_ARG, "FP64 path has one tile shape");
@@ -1312,6 +1371,8 @@ int ibfem_autotune(ibfem_t* h, int reps, int* variant, double* ms) {
     cudaEventDestroy(e1);
     best = t[1] < t[0] ? 1 : 0;
     h->set_tc_variant(best);
+  } else if (h->opt.precision == IBFEM_EXACT64_TC) {
+    best = h->tc_variant;   // one tile shape
   }
   if (variant) *variant = best;
   if (ms) {

@@ -52,8 +52,10 @@ struct Handle {
   void build_tc_tiles();
   void upload_tc_sources();
   void set_tc_variant(int v);
-  // tensor-core scheme: 0 exact digit slices, 1 bf16 three-pass, 2 bf16 one pass
-  int tc_scheme() const { return opt.precision == IBFEM_EXACT_TC ? 0 : (opt.precision == IBFEM_BF16X3_TC ? 1 : 2); }
+  // tensor-core scheme: 0 exact digit slices, 1 bf16 three-pass, 2 bf16 one pass, 3 FP64-grade
+  int tc_scheme() const {
+    return opt.precision == IBFEM_EXACT_TC ? 0 : opt.precision == IBFEM_BF16X3_TC ? 1 : opt.precision == IBFEM_EXACT64_TC ? 3 : 2;
+  }
   // IMEX (Algorithm 2): host partition/factor and their device copies
   bool imex = false;
   bool consistent = false;      // IBFEM_CDM_CONSISTENT: the IMEX machinery with beta = 0

@@ -21,10 +21,10 @@ STAB_NONE, STAB_EVS, STAB_MASS_SCALING = 0, 1, 2
 SCALAR, ELASTIC_PLANE_STRAIN = 0, 1
 CDM, IMEX, CDM_CONSISTENT = 0, 1, 2
 SCHEMES = {"cdm": CDM, "imex": IMEX, "cdm_consistent": CDM_CONSISTENT}
-FP64, EXACT_TC, BF16X3_TC, BF16_TC = 0, 1, 2, 3
+FP64, EXACT_TC, BF16X3_TC, BF16_TC, EXACT64_TC = 0, 1, 2, 3, 4
 SRC_NONE, SRC_POINT, SRC_EDGE_TRACTION, SRC_GAUSS = 0, 1, 2, 3
 
-PRECISIONS = {"fp64": FP64, "exact": EXACT_TC, "bf16x3": BF16X3_TC, "bf16": BF16_TC}
+PRECISIONS = {"fp64": FP64, "exact": EXACT_TC, "bf16x3": BF16X3_TC, "bf16": BF16_TC, "exact64": EXACT64_TC}
 
 
 class IbfemError(RuntimeError):
