@@ -43,9 +43,10 @@ using namespace tc;
 namespace {
 
 // Balanced 8-bit digits of round(|x| 2^(31 - E)) for an FP64 x whose biased exponent is at
-// most em (the row's largest), sign applied to every digit; 32-bit integer operations only.
-// d0 in [0, 256], d1..d3 in [-128, 128) before the sign.
-__device__ __forceinline__ void fp64_digits(double x, int em, int d[4]) {
+// most em (the tile's largest), sign applied to every digit, as four BF16 values (digits 0, 1
+// in .x, digits 2, 3 in .y, low half first); 32-bit integer operations only.  d0 in [0, 256],
+// d1..d3 in [-128, 128) before the sign.
+__device__ __forceinline__ uint2 fp64_digits_bf16(double x, int em) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const uint32_t hw = (uint32_t)(bits >> 32), lw = (uint32_t)bits;
   const int eb = (int)((hw >> 20) & 0x7ffu);
@@ -64,17 +65,19 @@ __device__ __forceinline__ void fp64_digits(double x, int em, int d[4]) {
       V = t + rb;
     }
   }
-  const int d0 = (int)((V >> 24) + ((V >> 23) & 1u));
-  int r = (int)(V - ((uint32_t)d0 << 24));          // in [-2^23, 2^23)
-  const int d1 = (r + 0x8000) >> 16;
-  r -= d1 << 16;
-  const int d2 = (r + 0x80) >> 8;
-  const int d3 = r - (d2 << 8);
-  const bool neg = (hw >> 31) != 0;
-  d[0] = neg ? -d0 : d0;
-  d[1] = neg ? -d1 : d1;
-  d[2] = neg ? -d2 : d2;
-  d[3] = neg ? -d3 : d3;
+  // balanced digits: the lower three are the bytes of (V mod 2^24) + 0x808080 minus 128
+  // (each in [-128, 127]); the carry out of them goes to the top digit (in [0, 256])
+  const uint32_t wl = (V & 0xFFFFFFu) + 0x808080u;
+  const int d0 = (int)(V >> 24) + (int)(wl >> 24);
+  // exact FP32 of byte b minus 128: the pattern 0x4B4000bb is the float 1.5 * 2^23 + b
+  const uint32_t f0 = f32_bits_of_small_int(d0);
+  const uint32_t f1 = __float_as_uint(__uint_as_float(__byte_perm(wl, 0x4B400000u, 0x7652)) - 12583040.0f);
+  const uint32_t f2 = __float_as_uint(__uint_as_float(__byte_perm(wl, 0x4B400000u, 0x7651)) - 12583040.0f);
+  const uint32_t f3 = __float_as_uint(__uint_as_float(__byte_perm(wl, 0x4B400000u, 0x7650)) - 12583040.0f);
+  // BF16 = upper half of the FP32 pattern (at most 8 significant bits: exact); the sign of
+  // x goes to every digit
+  const uint32_t sgn = (hw >> 31) ? 0x80008000u : 0u;
+  return make_uint2(__byte_perm(f0, f1, 0x7632) ^ sgn, __byte_perm(f2, f3, 0x7632) ^ sgn);
 }
 
 // Diagnostic of the bounded waits: one thread waits, with the poll limit given by the host,
@@ -427,10 +430,9 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
       double x = pf[i];
       uint32_t lo16, hi16;
       if (SCHEME == 0) {
-        int dg[4];
-        fp64_digits(x, em, dg);
-        lo16 = bf16x2_of_small_ints(dg[0], dg[1]);
-        hi16 = bf16x2_of_small_ints(dg[2], dg[3]);
+        const uint2 dg = fp64_digits_bf16(x, em);
+        lo16 = dg.x;
+        hi16 = dg.y;
       } else {
         float xf = f64_to_f32_rn(x);
         uint16_t h = bf16_rn(xf);
