@@ -137,7 +137,8 @@ typedef struct {
     int64_t n_elem, n_uncut, n_cut, n_outside;
     int64_t n_c;              /* IMEX: DOFs treated implicitly (0 for CDM)             */
     int64_t nnz_L;            /* IMEX: nonzeros of the Cholesky factor                 */
-    int32_t n_levels;         /* IMEX: level count of the forward solve                */
+    int32_t n_levels;         /* IMEX: sequential block steps of one triangular solve
+                                 (height groups of the largest component's supernodes)   */
     int32_t n_loc;            /* DOFs per element                                      */
     int32_t ncomp;
     int32_t precision;
@@ -240,8 +241,11 @@ int ibfem_step(ibfem_t* h, int64_t n);
 
 /* Same as ibfem_step, but every kernel is launched directly with a pair of CUDA events
  * around it on the handle's stream (no graph).  When flush_bytes > 0, flush_buf (device
- * memory of at least flush_bytes) is overwritten with cudaMemsetAsync before every step,
- * outside the timed events, to evict the L2 cache.  ms[0] accumulates the device time of
+ * memory of at least flush_bytes; each half larger than the L2 cache) evicts the L2 cache
+ * before every step, outside the timed events: its first half is overwritten with
+ * cudaMemsetAsync and its second half is then read by a kernel, so that the write-back of
+ * the dirty lines (the memset's and the previous step's) happens before the step and the
+ * step starts with the cache holding clean lines of unrelated data.  ms[0] accumulates the device time of
  * whole steps (first kernel start to last kernel end), ms[1 + k] that of kernel k (at most
  * max_slots values; names from ibfem_kernel_name); *n_slots receives the slot count.
  * Synchronises.  Library: meant for benchmarks and profiles.

@@ -915,17 +915,36 @@ namespace ibfem {
 
 namespace {
 
+// Supernode blocks of at most kMaxBlock rows: the GPU solves a block's dense diagonal part
+// from a warp's 32 x 32 shared-memory copy; longer runs become a chain of blocks of rising
+// height, whose couplings inside the run are off-block entries (solved row-parallel).
+constexpr int64_t kMaxBlock = 32;
+
+// Records a run of `size` consecutive rows as supernodes starting at height h0; returns the
+// height of its last block.
+int push_blocks(int64_t size, int h0, std::vector<std::array<int64_t, 2>>& blocks) {
+  int h = h0;
+  for (int64_t done = 0; done < size; done += kMaxBlock, ++h)
+    blocks.push_back({std::min(kMaxBlock, size - done), (int64_t)h});
+  return h - 1;
+}
+
 // Geometric nested dissection of one connected vertex set: split along the longest axis
 // at the median, take the vertices of the upper half adjacent to the lower half as the
-// separator, order lower half, upper half, separator (recursively).
-void nested_dissection(std::vector<int64_t>& verts, const std::vector<int64_t>& Ap,
-                       const std::vector<int64_t>& Ai, const std::vector<std::array<int64_t, 3>>& xyz,
-                       std::vector<int32_t>& tag, int32_t& next_tag, std::vector<int64_t>& out) {
+// separator, order lower half, upper half, separator (recursively).  The leaf blocks and
+// the separators are recorded as supernodes (size, height) in the same order; returns the
+// height of the set's top supernode (-1 for an empty set).
+int nested_dissection(std::vector<int64_t>& verts, const std::vector<int64_t>& Ap,
+                      const std::vector<int64_t>& Ai, const std::vector<std::array<int64_t, 3>>& xyz,
+                      std::vector<int32_t>& tag, int32_t& next_tag, std::vector<int64_t>& out,
+                      std::vector<std::array<int64_t, 2>>& blocks) {
   const size_t kLeaf = 24;
-  if (verts.size() <= kLeaf) {
+  if (verts.empty()) return -1;
+  auto leaf = [&]() {
     out.insert(out.end(), verts.begin(), verts.end());
-    return;
-  }
+    return push_blocks((int64_t)verts.size(), 0, blocks);
+  };
+  if (verts.size() <= kLeaf) return leaf();
   int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {INT64_MIN, INT64_MIN, INT64_MIN};
   for (int64_t v : verts)
     for (int k = 0; k < 3; ++k) {
@@ -935,10 +954,7 @@ void nested_dissection(std::vector<int64_t>& verts, const std::vector<int64_t>& 
   int axis = 0;
   for (int k = 1; k < 3; ++k)
     if (hi[k] - lo[k] > hi[axis] - lo[axis]) axis = k;
-  if (hi[axis] == lo[axis]) {
-    out.insert(out.end(), verts.begin(), verts.end());
-    return;
-  }
+  if (hi[axis] == lo[axis]) return leaf();
   std::sort(verts.begin(), verts.end(), [&](int64_t a, int64_t b) {
     return xyz[a][axis] != xyz[b][axis] ? xyz[a][axis] < xyz[b][axis] : a < b;
   });
@@ -958,14 +974,19 @@ void nested_dissection(std::vector<int64_t>& verts, const std::vector<int64_t>& 
       if (tag[Ai[p]] == tA) sep = true;
     (sep ? S : B).push_back(v);
   }
-  if (A.empty() || (B.empty() && S.size() == verts.size())) {
-    out.insert(out.end(), verts.begin(), verts.end());
-    return;
-  }
-  nested_dissection(A, Ap, Ai, xyz, tag, next_tag, out);
-  nested_dissection(B, Ap, Ai, xyz, tag, next_tag, out);
+  if (A.empty() || (B.empty() && S.size() == verts.size())) return leaf();
+  const int hA = nested_dissection(A, Ap, Ai, xyz, tag, next_tag, out, blocks);
+  const int hB = nested_dissection(B, Ap, Ai, xyz, tag, next_tag, out, blocks);
+  if (S.empty()) return std::max(hA, hB);
   out.insert(out.end(), S.begin(), S.end());
+  return push_blocks((int64_t)S.size(), 1 + std::max(hA, hB), blocks);
 }
+
+// The sparse Cholesky factorisation below (elimination tree with path compression over
+// ancestors, row patterns as reaches in that tree, up-looking factorisation one row of L at
+// a time) is the published algorithm of T. A. Davis, "Direct Methods for Sparse Linear
+// Systems", SIAM 2006, Ch. 4 (etree, ereach, up-looking Cholesky), in this library's data
+// layout: L kept by columns with the diagonal first, plus its CSR by rows.
 
 // Elimination tree of a symmetric matrix given by its full CSR pattern.
 void etree(int64_t n, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
@@ -1166,6 +1187,11 @@ void imex_partition(const Setup& s, ImexData& d) {
   int32_t next_tag = 0;
   d.perm.clear();
   d.comp_ptr.assign(1, 0);
+  d.sn_start.clear();
+  d.sn_size.clear();
+  d.sn_height.clear();
+  std::vector<std::array<int64_t, 2>> blocks;
+  int64_t sn_row = 0;
   std::vector<int64_t> queue;
   for (int64_t r = 0; r < d.n_c; ++r) {
     if (comp[r] >= 0) continue;
@@ -1180,7 +1206,14 @@ void imex_partition(const Setup& s, ImexData& d) {
           queue.push_back(d.Si[p]);
         }
     }
-    nested_dissection(queue, d.Sp, d.Si, xyz, tag, next_tag, d.perm);
+    blocks.clear();
+    nested_dissection(queue, d.Sp, d.Si, xyz, tag, next_tag, d.perm, blocks);
+    for (auto& b : blocks) {
+      d.sn_start.push_back(sn_row);
+      d.sn_size.push_back((int32_t)b[0]);
+      d.sn_height.push_back((int32_t)b[1]);
+      sn_row += b[0];
+    }
     d.comp_ptr.push_back((int32_t)d.perm.size());
   }
   d.iperm.assign(d.n_c, 0);
@@ -1229,34 +1262,72 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
   permuted(d, Sx, P, I, X);
   if (!sparse_cholesky(d.n_c, P, I, X, d.chol, err)) return false;
   d.beta_dt2 = beta_dt2;
-  // level schedules per component
+  // block solve data: each supernode's dense diagonal block of L, and where each row's
+  // entries leave its block (the rows of L and of L^T are sorted by column)
   const SparseChol& L = d.chol;
-  std::vector<int32_t> lf(d.n_c, 0), lb(d.n_c, 0);
-  for (int64_t r = 0; r < d.n_c; ++r)
-    for (int64_t p = L.Lp[r]; p + 1 < L.Lp[r + 1]; ++p) lf[r] = std::max(lf[r], lf[L.Li[p]] + 1);
-  for (int64_t r = d.n_c - 1; r >= 0; --r)
-    for (int64_t p = L.Up[r] + 1; p < L.Up[r + 1]; ++p) lb[r] = std::max(lb[r], lb[L.Ui[p]] + 1);
-  d.chol.fwd_level_ptr.assign(1, 0);
-  d.chol.bwd_level_ptr.assign(1, 0);
-  d.chol.fwd_rows.clear();
-  d.chol.bwd_rows.clear();
-  d.comp_flvl.assign(1, 0);
-  d.comp_blvl.assign(1, 0);
-  for (size_t c = 0; c + 1 < d.comp_ptr.size(); ++c) {
-    for (int pass = 0; pass < 2; ++pass) {
-      const std::vector<int32_t>& lv = pass == 0 ? lf : lb;
-      std::vector<int32_t>& rows = pass == 0 ? d.chol.fwd_rows : d.chol.bwd_rows;
-      std::vector<int32_t>& ptr = pass == 0 ? d.chol.fwd_level_ptr : d.chol.bwd_level_ptr;
-      int32_t nlev = 0;
-      for (int32_t r = d.comp_ptr[c]; r < d.comp_ptr[c + 1]; ++r) nlev = std::max(nlev, lv[r] + 1);
-      std::vector<std::vector<int32_t>> by(nlev);
-      for (int32_t r = d.comp_ptr[c]; r < d.comp_ptr[c + 1]; ++r) by[lv[r]].push_back(r);
-      for (auto& b : by) {
-        rows.insert(rows.end(), b.begin(), b.end());
-        ptr.push_back((int32_t)rows.size());
-      }
-      (pass == 0 ? d.comp_flvl : d.comp_blvl).push_back((int32_t)ptr.size() - 1);
+  const size_t nsn = d.sn_start.size();
+  d.sn_doff.assign(nsn + 1, 0);
+  for (size_t q = 0; q < nsn; ++q) d.sn_doff[q + 1] = d.sn_doff[q] + (int64_t)d.sn_size[q] * d.sn_size[q];
+  d.sn_D.assign((size_t)d.sn_doff[nsn], 0.0);
+  d.sn_DT.assign((size_t)d.sn_doff[nsn], 0.0);
+  d.f_off_end.assign(d.n_c, 0);
+  d.b_off_beg.assign(d.n_c, 0);
+  std::vector<double> Ls;
+  for (size_t q = 0; q < nsn; ++q) {
+    const int64_t st = d.sn_start[q], w = d.sn_size[q], en = st + w;
+    Ls.assign((size_t)w * w, 0.0);
+    for (int64_t r = st; r < en; ++r) {
+      int64_t p = L.Lp[r];
+      while (p < L.Lp[r + 1] && L.Li[p] < st) ++p;
+      d.f_off_end[r] = p;
+      for (; p < L.Lp[r + 1]; ++p) Ls[(size_t)(r - st) * w + (L.Li[p] - st)] = L.Lx[p];
+      int64_t pb = L.Up[r];
+      while (pb < L.Up[r + 1] && L.Ui[pb] < en) ++pb;
+      d.b_off_beg[r] = pb;
     }
+    // the dense block itself (substitution within it is backward stable, unlike an
+    // explicit inverse), row-major and transposed, with 1 / L_jj in the diagonal slots
+    double* D = &d.sn_D[(size_t)d.sn_doff[q]];
+    double* DT = &d.sn_DT[(size_t)d.sn_doff[q]];
+    for (int64_t i = 0; i < w; ++i)
+      for (int64_t j = 0; j <= i; ++j) {
+        const double v = i == j ? 1.0 / Ls[(size_t)i * w + i] : Ls[(size_t)i * w + j];
+        D[i * w + j] = v;
+        DT[j * w + i] = v;
+      }
+  }
+  // height groups per component (components own contiguous runs of supernodes)
+  d.comp_hg.assign(1, 0);
+  d.hg_sn_ptr.assign(1, 0);
+  d.hg_frow_ptr.assign(1, 0);
+  d.hg_brow_ptr.assign(1, 0);
+  d.hg_sn.clear();
+  d.hg_frows.clear();
+  d.hg_brows.clear();
+  size_t q0 = 0;
+  for (size_t c = 0; c + 1 < d.comp_ptr.size(); ++c) {
+    size_t q1 = q0;
+    while (q1 < nsn && d.sn_start[q1] < d.comp_ptr[c + 1]) ++q1;
+    int hmax = -1;
+    for (size_t q = q0; q < q1; ++q) hmax = std::max(hmax, d.sn_height[q]);
+    for (int h = 0; h <= hmax; ++h) {
+      bool any = false;
+      for (size_t q = q0; q < q1; ++q) {
+        if (d.sn_height[q] != h) continue;
+        any = true;
+        d.hg_sn.push_back((int32_t)q);
+        for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) {
+          if (d.f_off_end[r] > L.Lp[r]) d.hg_frows.push_back((int32_t)r);
+          if (L.Up[r + 1] > d.b_off_beg[r]) d.hg_brows.push_back((int32_t)r);
+        }
+      }
+      if (!any) continue;
+      d.hg_sn_ptr.push_back((int32_t)d.hg_sn.size());
+      d.hg_frow_ptr.push_back((int32_t)d.hg_frows.size());
+      d.hg_brow_ptr.push_back((int32_t)d.hg_brows.size());
+    }
+    d.comp_hg.push_back((int32_t)d.hg_sn_ptr.size() - 1);
+    q0 = q1;
   }
   return true;
 }

@@ -108,8 +108,6 @@ struct SparseChol {
   std::vector<double> Lx;
   std::vector<int64_t> Up, Ui;       // CSR of L^T (upper), diagonal first per row
   std::vector<double> Ux;
-  std::vector<int32_t> fwd_level_ptr, fwd_rows;  // level schedule of L y = b
-  std::vector<int32_t> bwd_level_ptr, bwd_rows;  // level schedule of L^T x = y
 };
 bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vector<int64_t>& Ai,
                      const std::vector<double>& Ax, SparseChol& out, std::string& err);
@@ -117,7 +115,7 @@ bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vecto
 // IMEX partition (Sec. 2.6, Algorithm 2): the c-set (DOFs with support in a cut cell),
 // the consistent M^cc and K^cc on it, and the Cholesky factor of S = M^cc + beta dt^2 K^cc
 // in a fill-reducing order (connected components, then geometric nested dissection), with
-// level schedules of the two triangular solves per component.
+// the supernodes of that order for the block triangular solves.
 struct ImexData {
   int64_t n_c = 0;
   std::vector<int64_t> c_dof;          // c index -> lattice DOF (lattice order)
@@ -134,8 +132,25 @@ struct ImexData {
   std::vector<int32_t> g_idx;
   // factor of S (rebuilt per dt)
   SparseChol chol;
-  std::vector<int32_t> comp_flvl, comp_blvl;   // per component: range into level pointers
   double beta_dt2 = 0.0;
+  // supernodes of the nested-dissection order (dt-independent): contiguous row ranges (the
+  // leaf blocks and the separators), each depending only on the supernodes below it in the
+  // dissection tree; height 0 for a leaf, one above its highest child for a separator
+  std::vector<int64_t> sn_start;
+  std::vector<int32_t> sn_size, sn_height;
+  // block solve data (rebuilt with the factor): per supernode its dense diagonal block of L
+  // (w x w, row-major, zeros above the diagonal, 1 / L_jj on it) and its transpose, at
+  // sn_doff; per row the end of its off-block part in the CSR of L (forward) and the start of
+  // its off-block part in the CSR of L^T (backward); per component its height groups, in
+  // increasing height, each a list of supernodes and a list of the rows that have off-block
+  // entries (forward / backward)
+  std::vector<int64_t> sn_doff;
+  std::vector<double> sn_D, sn_DT;
+  std::vector<int64_t> f_off_end, b_off_beg;
+  std::vector<int32_t> comp_hg;                 // per component: range of height groups
+  std::vector<int32_t> hg_sn_ptr, hg_sn;        // per group: supernodes
+  std::vector<int32_t> hg_frow_ptr, hg_frows;   // per group: rows with forward off-block entries
+  std::vector<int32_t> hg_brow_ptr, hg_brows;   // per group: rows with backward off-block entries
 };
 // Build the partition and the pattern (dt-independent part).
 void imex_partition(const Setup& s, ImexData& d);

@@ -93,10 +93,22 @@ struct ImexDev {
   const double* Lx;
   const int64_t *Up, *Ui;    // L^T by rows, diagonal first
   const double* Ux;
-  const double* dinv;        // 1 / L_rr
-  const int32_t *f_lvl, *f_rows, *comp_flvl;
-  const int32_t *b_lvl, *b_rows, *comp_blvl;
-  const int4 *f_sched, *b_sched;   // per level and warp: {row, first entry, end, rows in the level}
+  // block triangular solves: supernodes (contiguous permuted rows) with the inverse D of
+  // their dense diagonal block of L (row-major w x w at sn_doff) and its transpose DT; per
+  // row the end of its off-block entries in L and their start in L^T; per component its
+  // height groups, each a list of supernodes and the rows with forward / backward off-block
+  // entries
+  const int64_t* sn_start;
+  const int32_t* sn_w;
+  const int64_t* sn_doff;
+  const double* D;
+  const double* DT;
+  const int64_t* f_off_end;
+  const int64_t* b_off_beg;
+  const int32_t* comp_hg;
+  const int32_t *hg_sn_ptr, *hg_sn;
+  const int32_t *hg_frow_ptr, *hg_frows;
+  const int32_t *hg_brow_ptr, *hg_brows;
   const int64_t* perm;       // permuted row -> c index
   const int64_t* c_dof;      // c index -> lattice DOF
   double* vc;
@@ -137,6 +149,8 @@ cudaError_t launch_reduce_power(const double* partials, int nblocks, double* lam
                                 double* inv_norm, int iter, cudaStream_t st);
 cudaError_t launch_sample_now(const DevProblem& pb, const double* u, double* out, cudaStream_t st);
 int op_fp64_blocks(const DevProblem& pb);
+// L2 eviction before a timed step: memset of the first half of buf, read of the second half
+cudaError_t launch_l2_evict(void* buf, size_t bytes, cudaStream_t st);
 // Launchers (kernels_tc.cu)
 // scheme: 0 exact digit slices, 1 bf16 hi/lo three-pass, 2 bf16 one pass
 // variant: tile shape (0 full MMA tile, 1 small tile; 1 only with scheme 0)

@@ -7,8 +7,8 @@
 //                       FP64), x = [Psi_{k+1}^d ; Psi_pred^c];
 //   * imex_solve      : one CTA per connected component of the c-set: the residual
 //                       r = F^c_{k+1} - K^c Psi_pred gathered in a fixed order, the
-//                       level-scheduled forward and backward solves with the host Cholesky
-//                       factor of S = M^cc + beta dt^2 K^cc, and the Newmark correction
+//                       forward and backward solves with the host Cholesky factor of
+//                       S = M^cc + beta dt^2 K^cc by supernode blocks, and the Newmark correction
 //                       Psi''^c = S^{-1} r, Psi'^c = Psi'_pred^c + gamma dt Psi''^c,
 //                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c.  The last CTA advances the
 //                       step counter.
@@ -51,89 +51,80 @@ __global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, Ime
   }
 }
 
-// Level-scheduled triangular solve of one component (rows of a level are independent, one
-// warp per row, a block barrier between levels).  FWD: L y = b with the diagonal stored last
-// in each CSR row of L; else L^T x = y with the CSR rows of L^T, diagonal first.  The first
-// row of every warp in the next level -- its column indices, values (first 32) and 1/L_rr --
-// is fetched before the current level is solved, so after a barrier only the gathers of w
-// (shared memory when the component fits) remain on the critical path.
+// Block triangular solve of one component over the supernodes of its nested-dissection
+// order, one height group at a time (a supernode depends only on the supernodes below it in
+// the dissection tree, all in lower groups).  Per group: (1) every row with entries outside
+// its supernode subtracts them, w_r -= sum_j L_rj w_j (forward: columns j before the
+// supernode; backward, with L^T: rows j after it), one warp per row; (2) every supernode
+// (at most 32 rows) solves with its dense diagonal block of L by substitution, one warp per
+// supernode: the block is first copied to the warp's 32 x 32 shared-memory area with
+// independent coalesced loads, then the warp walks its columns (forward) or rows
+// (backward) while the lanes update the other rows; a block barrier after each part.
+// FWD: L y = b; else L^T x = y.
+constexpr int kSnMax = 32;   // rows of a supernode (the host splits longer runs)
+
 template <bool FWD>
-__device__ __forceinline__ void level_solve(int l0, int l1, const int4* __restrict__ sched,
-                                            const int32_t* __restrict__ lvl, const int32_t* __restrict__ rows,
-                                            const int64_t* __restrict__ P, const int64_t* __restrict__ I,
-                                            const double* __restrict__ X, const double* __restrict__ dinv,
-                                            double* w, int lane, int warp, int nwarps) {
-  // sched[lv * 32 + warp] = {row, first entry, end, rows in the level} of the warp's first row
-  // of level lv (row -1: none).  Software pipeline: the schedule entry of level lv + 2 and
-  // the entries (first 128) and 1/L_rr of level lv + 1 are loaded while level lv is solved,
-  // so after a barrier only the gathers of w (shared memory) wait.
-  constexpr int PF = 4;
-  const int4 none = make_int4(-1, 0, 0, 0);
-  int li[PF], li_n[PF];
-  double lx[PF], lx_n[PF], dv = 0.0, dv_n = 0.0;
-  auto load_row = [&](const int4 e, int* L, double* V, double& d) {
-    if (e.x < 0) return;
-#pragma unroll
-    for (int c = 0; c < PF; ++c) {
-      const int p = e.y + lane + 32 * c;
-      if (p < e.z) {
-        L[c] = (int)I[p];
-        V[c] = X[p];
-      }
-    }
-    d = dinv[e.x];
-  };
-  int4 sA = l0 < l1 ? sched[(size_t)l0 * 32 + warp] : none;
-  int4 sB = l0 + 1 < l1 ? sched[(size_t)(l0 + 1) * 32 + warp] : none;
-  load_row(sA, li, lx, dv);
-  for (int lv = l0; lv < l1; ++lv) {
-    const int4 sC = lv + 2 < l1 ? sched[(size_t)(lv + 2) * 32 + warp] : none;
-    load_row(sB, li_n, lx_n, dv_n);
-    if (sA.x >= 0) {
+__device__ __forceinline__ void block_solve(const ImexDev& im, int g0, int g1, double* w, double* scratch,
+                                            int lane, int warp, int nwarps) {
+  const int64_t* __restrict__ I = FWD ? im.Li : im.Ui;
+  const double* __restrict__ X = FWD ? im.Lx : im.Ux;
+  double* const S = scratch + warp * kSnMax * kSnMax;
+  for (int gi = 0; gi < g1 - g0; ++gi) {
+    const int g = FWD ? g0 + gi : g1 - 1 - gi;
+    const int32_t* rows = FWD ? im.hg_frows : im.hg_brows;
+    const int q0 = FWD ? im.hg_frow_ptr[g] : im.hg_brow_ptr[g];
+    const int q1 = FWD ? im.hg_frow_ptr[g + 1] : im.hg_brow_ptr[g + 1];
+    for (int q = q0 + warp; q < q1; q += nwarps) {
+      const int r = rows[q];
+      const int64_t a0 = FWD ? im.Lp[r] : im.b_off_beg[r];
+      const int64_t a1 = FWD ? im.f_off_end[r] : im.Up[r + 1];
       double acc = 0.0;
-#pragma unroll
-      for (int c = 0; c < PF; ++c)
-        if (sA.y + lane + 32 * c < sA.z) acc = fma(lx[c], w[li[c]], acc);
-      for (int p = sA.y + lane + 32 * PF; p < sA.z; p += 32) acc = fma(X[p], w[I[p]], acc);
+      for (int64_t p = a0 + lane; p < a1; p += 32) acc = fma(X[p], w[I[p]], acc);
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) w[sA.x] = (w[sA.x] - acc) * dv;
-    }
-    if (sA.w > nwarps) {   // levels wider than the warps: the other rows, fetched on demand
-      const int q0 = lvl[lv], q1 = lvl[lv + 1];
-      for (int q = q0 + warp + nwarps; q < q1; q += nwarps) {
-        const int rr = rows[q];
-        const int64_t a0 = FWD ? P[rr] : P[rr] + 1, a1 = FWD ? P[rr + 1] - 1 : P[rr + 1];
-        double acc = 0.0;
-        for (int64_t p = a0 + lane; p < a1; p += 32) acc = fma(X[p], w[I[p]], acc);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) w[rr] = (w[rr] - acc) * dinv[rr];
-      }
+      if (lane == 0) w[r] -= acc;
     }
     __syncthreads();
-    sA = sB;
-    sB = sC;
-#pragma unroll
-    for (int c = 0; c < PF; ++c) {
-      li[c] = li_n[c];
-      lx[c] = lx_n[c];
+    for (int q = im.hg_sn_ptr[g] + warp; q < im.hg_sn_ptr[g + 1]; q += nwarps) {
+      const int sn = im.hg_sn[q];
+      double* __restrict__ ws = w + im.sn_start[sn];
+      const int wd = im.sn_w[sn];
+      // forward: column j of the block is row j of DT; backward: row j of L_ss is row j of D
+      const double* __restrict__ M = (FWD ? im.DT : im.D) + im.sn_doff[sn];
+      for (int e = lane; e < wd * wd; e += 32) S[e] = M[e];
+      __syncwarp();
+      for (int jj = 0; jj < wd; ++jj) {
+        const int j = FWD ? jj : wd - 1 - jj;
+        const double* Sj = S + j * wd;
+        const double xj = ws[j] * Sj[j];   // Sj[j] = 1 / L_jj
+        __syncwarp();
+        if (lane == 0) ws[j] = xj;
+        const int i = lane;
+        if (FWD ? (i > j && i < wd) : (i < j)) ws[i] = fma(-Sj[i], xj, ws[i]);
+        __syncwarp();
+      }
+      __syncwarp();   // the scratch is reused by the warp's next supernode
     }
-    dv = dv_n;
+    __syncthreads();
   }
 }
 
 // A component's rows only couple to rows of the same component, so its vector can live in
 // shared memory, indexed by the permuted row (w = smem - r0).
+// The first kImexWarps * 32 * 32 doubles of the dynamic shared memory are the warps'
+// supernode scratch areas, the component's vector (when it fits) follows.
 extern __shared__ double imex_smem[];
+constexpr int kImexThreads = 512;
+constexpr int kImexScratch = kImexThreads / 32 * kSnMax * kSnMax;
 
-__global__ void __launch_bounds__(1024) imex_solve_kernel(DevProblem pb, ImexDev im, double* __restrict__ out,
-                                                          int in_smem) {
+__global__ void __launch_bounds__(kImexThreads) imex_solve_kernel(DevProblem pb, ImexDev im, double* __restrict__ out,
+                                                                  int in_smem) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int r0 = im.comp_ptr[b], r1 = im.comp_ptr[b + 1];
   const unsigned long long k = *((volatile unsigned long long*)pb.step);
   double fk1 = 0.0;
   if (pb.f_e > 0.0 && im.Fc) fk1 = ricker_imex((double)(k + 1) * pb.dt, pb.f_e);
-  double* w = in_smem ? imex_smem - r0 : im.work;
+  double* w = in_smem ? imex_smem + kImexScratch - r0 : im.work;
   // residual r = F_{k+1}^c - K^c Psi_pred (fixed summation order)
   for (int r = r0 + tid; r < r1; r += blockDim.x) {
     double acc = im.Fc ? im.Fc[r] * fk1 : 0.0;
@@ -141,11 +132,9 @@ __global__ void __launch_bounds__(1024) imex_solve_kernel(DevProblem pb, ImexDev
     w[r] = acc;
   }
   __syncthreads();
-  // L y = r, then L^T x = y, level by level
-  level_solve<true>(im.comp_flvl[b], im.comp_flvl[b + 1], im.f_sched, im.f_lvl, im.f_rows, im.Lp, im.Li, im.Lx,
-                    im.dinv, w, lane, warp, nwarps);
-  level_solve<false>(im.comp_blvl[b], im.comp_blvl[b + 1], im.b_sched, im.b_lvl, im.b_rows, im.Up, im.Ui, im.Ux,
-                     im.dinv, w, lane, warp, nwarps);
+  // L y = r, then L^T x = y, by supernode height groups
+  block_solve<true>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
+  block_solve<false>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
   // Newmark correction on the c-DOFs
   bool bad = false;
   for (int r = r0 + tid; r < r1; r += blockDim.x) {
@@ -175,34 +164,33 @@ __global__ void __launch_bounds__(1024) imex_solve_kernel(DevProblem pb, ImexDev
 // iteration of the consistent-mass CDM (S = M^cc there): one CTA per component; the right-
 // hand side is b[r] = in[c_dof[perm[r]]] * scal, the solution of L w = b (forward) or of
 // L^T w = b (backward) is written to out[c_dof[perm[r]]].
-__global__ void __launch_bounds__(1024, 1) imex_tri_kernel(ImexDev im, const double* __restrict__ in,
+__global__ void __launch_bounds__(kImexThreads, 1) imex_tri_kernel(ImexDev im, const double* __restrict__ in,
                                                         const double* __restrict__ scal,
                                                         double* __restrict__ out, int backward, int in_smem) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int r0 = im.comp_ptr[b], r1 = im.comp_ptr[b + 1];
   const double sc = scal ? *scal : 1.0;
-  double* w = in_smem ? imex_smem - r0 : im.work;
+  double* w = in_smem ? imex_smem + kImexScratch - r0 : im.work;
   for (int r = r0 + tid; r < r1; r += blockDim.x) w[r] = in[im.c_dof[im.perm[r]]] * sc;
   __syncthreads();
   if (!backward)
-    level_solve<true>(im.comp_flvl[b], im.comp_flvl[b + 1], im.f_sched, im.f_lvl, im.f_rows, im.Lp, im.Li, im.Lx,
-                      im.dinv, w, lane, warp, nwarps);
+    block_solve<true>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
   else
-    level_solve<false>(im.comp_blvl[b], im.comp_blvl[b + 1], im.b_sched, im.b_lvl, im.b_rows, im.Up, im.Ui, im.Ux,
-                       im.dinv, w, lane, warp, nwarps);
+    block_solve<false>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
   for (int r = r0 + tid; r < r1; r += blockDim.x) out[im.c_dof[im.perm[r]]] = w[r];
 }
 
-// dynamic shared memory for the largest component's vector (0: the global work vector)
-static size_t imex_smem_bytes(const ImexDev& im) {
+// dynamic shared memory: the warps' scratch, then the largest component's vector if it fits
+// (else the vector stays in the global work array)
+static size_t imex_vec_bytes(const ImexDev& im) {
   const size_t bytes = (size_t)im.max_comp * sizeof(double);
-  return bytes <= (size_t)200 * 1024 ? bytes : 0;
+  return bytes + kImexScratch * sizeof(double) <= (size_t)220 * 1024 ? bytes : 0;
 }
 
 template <typename KernelT>
 static cudaError_t imex_smem_config(KernelT kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
 cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* scal, double* out, bool backward,
@@ -210,8 +198,9 @@ cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* s
   if (im.n_comp == 0) return cudaSuccess;
   static const cudaError_t cfg = imex_smem_config(imex_tri_kernel);
   if (cfg != cudaSuccess) return cfg;
-  const size_t sm = imex_smem_bytes(im);
-  imex_tri_kernel<<<im.n_comp, 1024, sm, st>>>(im, in, scal, out, backward ? 1 : 0, sm > 0 ? 1 : 0);
+  const size_t vb = imex_vec_bytes(im);
+  imex_tri_kernel<<<im.n_comp, kImexThreads, kImexScratch * sizeof(double) + vb, st>>>(im, in, scal, out,
+                                                                                     backward ? 1 : 0, vb > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -236,8 +225,8 @@ cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* o
   if (im.n_comp == 0) return cudaSuccess;
   static const cudaError_t cfg = imex_smem_config(imex_solve_kernel);
   if (cfg != cudaSuccess) return cfg;
-  const size_t sm = imex_smem_bytes(im);
-  imex_solve_kernel<<<im.n_comp, 1024, sm, st>>>(pb, im, out, sm > 0 ? 1 : 0);
+  const size_t vb = imex_vec_bytes(im);
+  imex_solve_kernel<<<im.n_comp, kImexThreads, kImexScratch * sizeof(double) + vb, st>>>(pb, im, out, vb > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 

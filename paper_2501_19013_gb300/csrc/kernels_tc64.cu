@@ -140,8 +140,10 @@ struct Tc64Cfg {
 };
 
 // One CTA per SM takes tiles from the global counter (CTA b starts with tile b); mode is
-// kModeCDM, kModeStartup or kModeApply.  The cut-cell products pb.Ycut of this step must be
-// in global memory before the launch.
+// kModeCDM, kModeStartup, kModeApply or kModeImex (Algorithm 2's explicit part: the CDM
+// update on the d-DOFs, which only uncut cells carry, and the Newmark predictor on the
+// c-DOFs, marked by dt^2/m = -(c + 1)).  Except in kModeImex the cut-cell products pb.Ycut
+// of this input must be in global memory before the launch.
 template <int DIM, int P, int NC>
 __global__ void __launch_bounds__(kThreads64, 1) op_tc64_kernel(const __grid_constant__ DevProblem pb,
                                                              const double* __restrict__ u,
@@ -248,7 +250,9 @@ __global__ void __launch_bounds__(kThreads64, 1) op_tc64_kernel(const __grid_con
   unsigned long long k = 0;
   if (mode == kModeCDM) k = *((volatile unsigned long long*)pb.step);
   double fk = 0.0;
-  if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) fk = ricker_tc((double)k * pb.dt, pb.f_e);
+  if (mode == kModeImex) k = *((volatile unsigned long long*)pb.step);
+  if ((mode == kModeCDM || mode == kModeStartup || mode == kModeImex) && pb.tsrc_ptr && pb.f_e > 0.0)
+    fk = ricker_tc((double)k * pb.dt, pb.f_e);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(kThreads64, 1) op_tc64_kernel(const __grid_con
     if (tid < C::NE) {
       const int64_t cell = halo_cell(tile, tid);
       const int cl = cell < 0 ? 0 : (int)pb.cls[cell];
-      cidx[tid] = cl == 1 ? pb.cut_index[cell] : -1;
+      cidx[tid] = cl == 1 && mode != kModeImex ? pb.cut_index[cell] : -1;
       if (cl != 2) special[atomicAdd(n_special, 1)] = tid | (cl << 8);
     }
     // ---- tile exponent, then the seven digits of every patch value
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(kThreads64, 1) op_tc64_kernel(const __grid_con
     // ---- assembly (integer node sums, owned nodes as in kernels_tc.cu) and the FP64 update
     const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
     int src_lo = 0, src_hi = 0;
-    if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) {
+    if ((mode == kModeCDM || mode == kModeStartup || mode == kModeImex) && pb.tsrc_ptr && pb.f_e > 0.0) {
       src_lo = pb.tsrc_ptr[tile];
       src_hi = pb.tsrc_ptr[tile + 1];
     }
@@ -445,10 +449,18 @@ __global__ void __launch_bounds__(kThreads64, 1) op_tc64_kernel(const __grid_con
         out[dof] = f64_scale2(hd + td, zku) + yc;
         return;
       }
+      if (mode == kModeImex && mi < 0.0) {
+        // c-DOF: Newmark predictor of Algorithm 2 (its K u is taken by the c-set solve)
+        const int64_t ci = (int64_t)(-mi) - 1;
+        const double a = pb.imex_ac[ci], v = pb.imex_vc[ci];
+        out[dof] = uval + pb.dt * v + pb.imex_c1 * a;
+        pb.imex_vc[ci] = v + pb.imex_c2 * a;
+        return;
+      }
       if (!(mi > 0.0)) return;
       const double c = -f64_scale2(mi, zku);   // -(dt^2 / m) 2^zku
       double r;
-      if (mode == kModeCDM)
+      if (mode == kModeCDM || mode == kModeImex)
         r = fma(c, hd, fma(c, td, fma(-mi, yc, fma(2.0, uval, -upv))));
       else
         r = fma(0.5 * c, hd, fma(0.5 * c, td, fma(-0.5 * mi, yc, fma(-pb.dt, upv, uval))));
@@ -546,7 +558,7 @@ __global__ void __launch_bounds__(kThreads64, 1) op_tc64_kernel(const __grid_con
     // the load F_k of this tile's DOFs, added after the update in FP64
     if (src_lo < src_hi && mode != kModeApply) {
       __syncthreads();
-      const double w = mode == kModeCDM ? 1.0 : 0.5;
+      const double w = mode == kModeStartup ? 0.5 : 1.0;
       for (int s2 = src_lo + tid; s2 < src_hi; s2 += NT) {
         const int64_t dof = pb.tsrc_dof[s2];
         const double mi = pb.minv[dof];

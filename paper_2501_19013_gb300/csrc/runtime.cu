@@ -475,50 +475,32 @@ void Handle::imex_upload_factor() {
   ImexDev& D = imex_dev;
   size_t nnz = L.Lx.size();
   if (imex_nnz_alloc != nnz) {
-    // the pattern and order do not depend on dt: allocated once
+    // the pattern, the order and the supernodes do not depend on dt: allocated once
+    const size_t nd = I.sn_D.size();
     D.Lp = static_cast<int64_t*>(dalloc((I.n_c + 1) * sizeof(int64_t)));
     D.Li = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t)));
     D.Lx = static_cast<double*>(dalloc(nnz * sizeof(double)));
     D.Up = static_cast<int64_t*>(dalloc((I.n_c + 1) * sizeof(int64_t)));
     D.Ui = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t)));
     D.Ux = static_cast<double*>(dalloc(nnz * sizeof(double)));
-    D.dinv = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
-    D.f_lvl = upload(L.fwd_level_ptr);
-    D.f_rows = upload(L.fwd_rows);
-    D.b_lvl = upload(L.bwd_level_ptr);
-    D.b_rows = upload(L.bwd_rows);
-    D.comp_flvl = upload(I.comp_flvl);
-    D.comp_blvl = upload(I.comp_blvl);
+    D.D = static_cast<double*>(dalloc(std::max<size_t>(nd, 1) * sizeof(double)));
+    D.DT = static_cast<double*>(dalloc(std::max<size_t>(nd, 1) * sizeof(double)));
+    D.f_off_end = static_cast<int64_t*>(dalloc(I.n_c * sizeof(int64_t)));
+    D.b_off_beg = static_cast<int64_t*>(dalloc(I.n_c * sizeof(int64_t)));
+    D.sn_start = upload(I.sn_start);
+    D.sn_w = upload(I.sn_size);
+    D.sn_doff = upload(I.sn_doff);
+    D.comp_hg = upload(I.comp_hg);
+    D.hg_sn_ptr = upload(I.hg_sn_ptr);
+    D.hg_sn = upload(I.hg_sn);
+    D.hg_frow_ptr = upload(I.hg_frow_ptr);
+    D.hg_frows = upload(I.hg_frows);
+    D.hg_brow_ptr = upload(I.hg_brow_ptr);
+    D.hg_brows = upload(I.hg_brows);
     imex_nnz_alloc = nnz;
   }
-  std::vector<double> dinv(I.n_c);
-  for (int64_t r = 0; r < I.n_c; ++r) dinv[r] = 1.0 / L.Ux[L.Up[r]];
-  // per level and warp (32 per CTA): the warp's first row of the level with its entry range
-  // (forward: L rows without the trailing diagonal; backward: L^T rows without the leading one)
-  auto sched = [&](const std::vector<int32_t>& lp, const std::vector<int32_t>& lr, bool fwd) {
-    const size_t nl = lp.size() - 1;
-    std::vector<int32_t> v(nl * 32 * 4, 0);
-    for (size_t lv = 0; lv < nl; ++lv)
-      for (int wq = 0; wq < 32; ++wq) {
-        int32_t* e = &v[(lv * 32 + wq) * 4];
-        const int q = lp[lv] + wq;
-        e[3] = lp[lv + 1] - lp[lv];
-        if (q >= lp[lv + 1]) {
-          e[0] = -1;
-          continue;
-        }
-        const int r = lr[q];
-        e[0] = r;
-        e[1] = (int32_t)(fwd ? L.Lp[r] : L.Up[r] + 1);
-        e[2] = (int32_t)(fwd ? L.Lp[r + 1] - 1 : L.Up[r + 1]);
-      }
-    return v;
-  };
-  if (nnz > (size_t)INT32_MAX) throw std::runtime_error("IMEX factor too large for 32-bit schedule entries");
-  D.f_sched = reinterpret_cast<const int4*>(upload(sched(L.fwd_level_ptr, L.fwd_rows, true)));
-  D.b_sched = reinterpret_cast<const int4*>(upload(sched(L.bwd_level_ptr, L.bwd_rows, false)));
   auto cp = [&](const void* dst, const void* src, size_t bytes) {
-    check(cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, stream), "factor upload");
+    if (bytes) check(cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, stream), "factor upload");
   };
   cp(D.Lp, L.Lp.data(), L.Lp.size() * sizeof(int64_t));
   cp(D.Li, L.Li.data(), nnz * sizeof(int64_t));
@@ -526,7 +508,10 @@ void Handle::imex_upload_factor() {
   cp(D.Up, L.Up.data(), L.Up.size() * sizeof(int64_t));
   cp(D.Ui, L.Ui.data(), nnz * sizeof(int64_t));
   cp(D.Ux, L.Ux.data(), nnz * sizeof(double));
-  cp(D.dinv, dinv.data(), dinv.size() * sizeof(double));
+  cp(D.D, I.sn_D.data(), I.sn_D.size() * sizeof(double));
+  cp(D.DT, I.sn_DT.data(), I.sn_DT.size() * sizeof(double));
+  cp(D.f_off_end, I.f_off_end.data(), I.f_off_end.size() * sizeof(int64_t));
+  cp(D.b_off_beg, I.b_off_beg.data(), I.b_off_beg.size() * sizeof(int64_t));
   check(cudaStreamSynchronize(stream), "factor upload");
 }
 
@@ -575,7 +560,7 @@ void Handle::timed_collect() {
 
 // One CDM step with u = U[cur], out = U[1 - cur] (in place over u^{k-1}).
 void Handle::enqueue_step(int cur) {
-  if (opt.precision == IBFEM_EXACT64_TC) {
+  if (opt.precision == IBFEM_EXACT64_TC && !imex) {
     // FP64-grade tensor-core step: the FP64 cut-cell products (and the observers), then the
     // fused tensor-core operator and update
     OpInput x{U[cur], nullptr, nullptr};
@@ -591,7 +576,7 @@ void Handle::enqueue_step(int cur) {
     if (timing) step_last_ev.push_back(ev_used - 1);
     return;
   }
-  if (opt.precision != IBFEM_FP64) {
+  if (opt.precision != IBFEM_FP64 && opt.precision != IBFEM_EXACT64_TC) {
     slot_name[1] = tc_scheme() == 0 ? "op_tc_exact_fused_cdm" : (tc_scheme() == 1 ? "op_tc_bf16x3_fused_cdm" : "op_tc_bf16_fused_cdm");
     if (timing) step_first_ev.push_back(ev_used);
     timed_begin(1);
@@ -601,9 +586,12 @@ void Handle::enqueue_step(int cur) {
     return;
   }
   if (imex) {
+    // Algorithm 2: the explicit part (d-DOF update and c-DOF predictor) by the FP64 kernel or
+    // by the FP64-grade tensor-core kernel, then the c-cells' products and the c-set solve
+    const bool tc = opt.precision == IBFEM_EXACT64_TC;
     OpInput x{U[cur], nullptr, nullptr};
     slot_name[1] = "observers";
-    slot_name[2] = "op_fp64_fused_imex_explicit";
+    slot_name[2] = tc ? "op_tc_exact64_fused_imex_explicit" : "op_fp64_fused_imex_explicit";
     slot_name[3] = "imex_cell_apply";
     slot_name[4] = "imex_solve";
     if (timing) step_first_ev.push_back(ev_used);
@@ -611,7 +599,10 @@ void Handle::enqueue_step(int cur) {
     check(launch_cut_apply_fp64(dev, x, true, stream, false), "observers");
     timed_end();
     timed_begin(2);
-    check(launch_op_fp64(dev, x, U[1 - cur], kModeImex, nullptr, stream), "op_imex");
+    if (tc)
+      check(launch_op_tc64(dev, U[cur], U[1 - cur], kModeImex, stream), "op_tc64_imex");
+    else
+      check(launch_op_fp64(dev, x, U[1 - cur], kModeImex, nullptr, stream), "op_imex");
     timed_end();
     timed_begin(3);
     check(launch_imex_cell_apply(dev, imex_dev, U[1 - cur], stream), "imex_cells");
@@ -753,8 +744,8 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
     throw std::invalid_argument("unknown physics");
   if (o.scheme != IBFEM_CDM && o.scheme != IBFEM_IMEX && o.scheme != IBFEM_CDM_CONSISTENT)
     throw std::invalid_argument("unknown scheme");
-  if (o.scheme != IBFEM_CDM && o.precision != IBFEM_FP64)
-    throw std::invalid_argument("IMEX and the consistent-mass CDM run in FP64 (precision must be IBFEM_FP64)");
+  if (o.scheme != IBFEM_CDM && o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT64_TC)
+    throw std::invalid_argument("IMEX and the consistent-mass CDM run at FP64 grade (precision IBFEM_FP64 or IBFEM_EXACT64_TC)");
   in.need_consistent_mass = o.scheme != IBFEM_CDM;
   if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
       o.precision != IBFEM_BF16_TC && o.precision != IBFEM_EXACT64_TC)
@@ -900,7 +891,10 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
   if (h->imex) {
     out->n_c = h->imex_host.n_c;
     out->nnz_L = (int64_t)h->imex_host.chol.Lx.size();
-    out->n_levels = (int32_t)h->imex_host.chol.fwd_level_ptr.size() - 1;
+    int32_t steps = 0;   // height groups of the largest component: sequential steps of a solve
+    const ImexData& I = h->imex_host;
+    for (size_t c = 0; c + 1 < I.comp_hg.size(); ++c) steps = std::max(steps, I.comp_hg[c + 1] - I.comp_hg[c]);
+    out->n_levels = steps;
   }
   out->shared_device_bytes = h->shared ? h->shared->bytes : 0;
   out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes + out->shared_device_bytes;
@@ -1185,7 +1179,7 @@ int ibfem_step_timed(ibfem_t* h, int64_t n, void* flush_buf, size_t flush_bytes,
   for (double& v : h->slot_ms) v = 0.0;
   h->timing = true;
   for (int64_t i = 0; i < n; ++i) {
-    if (flush_bytes > 0) check(cudaMemsetAsync(flush_buf, (int)(i & 0xff), flush_bytes, h->stream), "flush");
+    if (flush_bytes > 0) check(launch_l2_evict(flush_buf, flush_bytes, h->stream), "flush");
     h->enqueue_step(h->cur);
     h->cur ^= 1;
     if (h->ev_used > 512) h->timed_collect();
