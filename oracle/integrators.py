@@ -141,8 +141,10 @@ class ImexSystem:
         self.dt = dt
 
 
-def imex(sys_, nsteps, u0=None, v0=None, F=None, f_e=None, obs=None, gamma=0.5):
-    """Algorithm 2 (beta = 1/4, gamma = 1/2)."""
+def imex(sys_, nsteps, u0=None, v0=None, F=None, f_e=None, obs=None, gamma=0.5, solver="lu"):
+    """Algorithm 2 (beta = 1/4, gamma = 1/2).  ``solver`` solves S a = r by a sparse LU
+    factorisation ("lu", SuperLU) or a dense Cholesky factorisation ("cholesky", LAPACK; small
+    c-sets): two backward-stable solvers whose difference measures the conditioning of S."""
     n, dt, beta = sys_.n, sys_.dt, sys_.beta
     d, c = sys_.d, sys_.c
     u = np.zeros(n) if u0 is None else np.asarray(u0, float).copy()
@@ -151,7 +153,18 @@ def imex(sys_, nsteps, u0=None, v0=None, F=None, f_e=None, obs=None, gamma=0.5):
     def load(t):
         return np.zeros(n) if F is None else F * ricker(t, f_e)
 
-    Sfac = spla.splu(sys_.S) if len(c) else None
+    Sfac = None
+    if len(c) and solver == "cholesky":
+        import scipy.linalg as sla
+        cf = sla.cho_factor(sys_.S.toarray(), lower=True)
+
+        class _Chol:
+            def solve(self, b):
+                return sla.cho_solve(cf, b)
+
+        Sfac = _Chol()
+    elif len(c):
+        Sfac = spla.splu(sys_.S)
     F0 = load(0.0)
     # CDM history for the d part (start-up as in cdm)
     minv_d = 1.0 / sys_.Mdd

@@ -9,11 +9,14 @@ from paper_2501_19013_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-# With alpha = 1e-12 (the paper's IMEX setting) S = M^cc + dt^2/4 K^cc carries eigenvalues of
-# order alpha next to O(1) ones; two backward-stable solvers (GPU Cholesky in nested-dissection
-# order, oracle sparse LU) then agree only to about cond(S) * eps per solve.  The strict FP64
-# bound is checked at alpha = 1e-4 and the alpha = 1e-12 cases get the conditioning bound.
-TOL_ILL = 1e-5
+# With alpha = 1e-12 (the paper's IMEX setting) S = M^cc + dt^2/4 K^cc is ill-conditioned
+# (on the 40^2 p = 3 case: cond(S) = 1.6e13, 8.8e8 after diagonal scaling), so two backward-
+# stable solvers of S agree only to about cond(S) eps per solve.  The bound there is
+# measured, not assumed: the oracle runs Algorithm 2 twice, with a sparse LU and with a dense
+# Cholesky factorisation of S, and the GPU (Cholesky in nested-dissection order) must agree
+# with both to within 30 times their spread (3.1e-8 on that case).  The strict FP64 bound is
+# checked at alpha = 1e-4, where the spread is 6e-14.
+SPREAD_FACTOR = 30.0
 IMEX_CASES = {
     "imex_scalar_p3": lambda: W.plate_holes_imex(n=40, p=3, count=3, seed=1, steps=150).with_(alpha=1e-4),
     "imex_scalar_p2_ragged": lambda: W.plate_holes_imex(n=27, p=2, count=2, seed=5, steps=120).with_(alpha=1e-4),
@@ -31,21 +34,24 @@ def d_block_lambda(d):
     return np.linalg.eigvalsh(A).max(), mask
 
 
-def oracle_imex(w, d, dt, steps, u0=None, v0=None):
+def oracle_imex(w, d, dt, steps, u0=None, v0=None, solver="lu"):
     F = OD.source_vector(d, w.source) if w.source else None
     obs = d.observer_matrix(w.observers)
     sys_ = OI.ImexSystem(d.K, d.ML, d.consistent_mass(), d.c_dofs(), dt)
-    return OI.imex(sys_, steps, u0=u0, v0=v0, F=F, f_e=w.f0, obs=obs)
+    return OI.imex(sys_, steps, u0=u0, v0=v0, F=F, f_e=w.f0, obs=obs, solver=solver)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "exact64"])
 @pytest.mark.parametrize("case", sorted(IMEX_CASES))
-def test_imex_run_matches_oracle(case):
+def test_imex_run_matches_oracle(case, precision):
+    """Algorithm 2 with its explicit part on the FP64 kernel or on the FP64-grade tensor-core
+    kernel, the c-set by the block Cholesky solves."""
     w = IMEX_CASES[case]()
     d = oracle_disc(w)
     lam_d, _ = d_block_lambda(d)
     dt = 0.9 * eigen.dt_crit(lam_d)
     u_o, s_o = oracle_imex(w, d, dt, w.steps)
-    s = gpu_solver(w)
+    s = gpu_solver(w, precision)
     inf = s.info()
     assert inf.n_c == len(d.c_dofs())
     s.set_dt(dt)
@@ -54,9 +60,15 @@ def test_imex_run_matches_oracle(case):
     s.sync()
     u_g, _ = s.get_state()
     s_g = s.sample(w.steps + 1)
-    tol = TOL if w.alpha >= 1e-4 else TOL_ILL
-    assert rel_l2(u_g, u_o) <= tol
-    assert rel_l2(s_g, s_o) <= tol
+    refs = [(u_o, s_o)]
+    tol = TOL
+    if w.alpha < 1e-4:
+        u_c, s_c = oracle_imex(w, d, dt, w.steps, solver="cholesky")
+        tol = max(TOL, SPREAD_FACTOR * rel_l2(u_c, u_o))
+        refs.append((u_c, s_c))
+    for u_r, s_r in refs:
+        assert rel_l2(u_g, u_r) <= tol
+        assert rel_l2(s_g, s_r) <= tol
     assert s.info().step == w.steps
     s.close()
 
@@ -146,8 +158,9 @@ def dense_lambda_gen(K, M):
     return sla.eigh(K.toarray(), M.toarray(), eigvals_only=True).max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "exact64"])
 @pytest.mark.parametrize("case", sorted(CONS_CASES))
-def test_consistent_cdm_run_matches_oracle(case):
+def test_consistent_cdm_run_matches_oracle(case, precision):
     w = CONS_CASES[case]()
     d = oracle_disc(w)
     stab = w.stab == "evs"
@@ -157,7 +170,7 @@ def test_consistent_cdm_run_matches_oracle(case):
     obs = d.observer_matrix(w.observers)
     sys_ = OI.ImexSystem(d.K, d.ML, d.consistent_mass(stabilised=stab), c, dt, beta=0.0)
     u_o, s_o = OI.imex(sys_, w.steps, F=F, f_e=w.f0, obs=obs)
-    s = gpu_solver(w)
+    s = gpu_solver(w, precision)
     assert s.info().n_c == len(c)
     s.set_dt(dt)
     s.set_initial()
@@ -166,7 +179,13 @@ def test_consistent_cdm_run_matches_oracle(case):
     u_g, _ = s.get_state()
     s_g = s.sample(w.steps + 1)
     assert rel_l2(u_g, u_o) <= TOL
-    assert rel_l2(s_g, s_o) <= TOL
+    if precision == "fp64":
+        assert rel_l2(s_g, s_o) <= TOL
+    else:
+        # the FP64-grade contraction is accurate relative to each tile's largest value, so an
+        # observer the wave has barely reached (here 5e-9 against a field of 1e-3) is checked
+        # element by element against the field's scale
+        assert np.abs(s_g - s_o).max() <= TOL * np.abs(u_o).max()
     s.close()
 
 

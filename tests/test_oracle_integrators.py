@@ -252,3 +252,17 @@ def test_threaded_matvec_and_pooled_setup_are_bitwise_serial():
     l1 = eigen.power_iteration(d1.K, d1.ML, max_iter=50)
     l2 = eigen.power_iteration(d1.K, d1.ML, max_iter=50, threads=4)
     assert l1 == l2
+
+
+def test_imex_lu_and_cholesky_solvers_agree_when_well_conditioned():
+    """Algorithm 2 with S solved by sparse LU or by dense Cholesky: the same scheme, so at
+    alpha = 1e-4 (S well conditioned) the two runs agree to rounding."""
+    d = small(p=3, n=6, alpha=1e-4)
+    c = d.c_dofs()
+    dt = 0.5 * eigen.dt_crit(eigen.dense_lambda_max(d.K, d.ML))
+    sys_ = OI.ImexSystem(d.K, d.ML, d.consistent_mass(), c, dt)
+    rng = np.random.default_rng(2)
+    u0 = rng.standard_normal(d.n_dof)
+    a, _ = OI.imex(sys_, 40, u0=u0)
+    b, _ = OI.imex(sys_, 40, u0=u0, solver="cholesky")
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
