@@ -7,7 +7,8 @@ traction, dt = 0.9 dt_crit.  One "step" is one central-difference time step (Eq.
 cut-cell mat-vec + fused element operator / assembly / update.
 
 Metric: DOF-steps/s (kept DOFs x steps / device time).  Every timed step is preceded by an
-untimed 256 MiB device write that evicts the L2 cache (the state of this workload, ~60 MB,
+untimed L2 eviction: a 256 MiB device write followed by a 256 MiB read of another buffer
+(so that the cache holds clean lines of unrelated data; the state of this workload, ~60 MB,
 would otherwise stay L2-resident).  Also reported: per-variant error against the FP64 path
 after the configured 10k steps and time to that accuracy, the dominant kernel's roofline,
 an end-to-end number through the C ABI with host buffers, the oracle timed on the host
@@ -37,7 +38,7 @@ if ROOT not in sys.path:
 METRIC = "DOF-steps/s & time to L2 err 1e-4 (mixed vs FP64 plain, 1 GB300); p50/p99 latency"
 UNIT = "DOF-steps/s"
 FP64_PEAK_GFLOPS = 1250.0   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal table figure)
-FLUSH_BYTES = 256 << 20
+FLUSH_BYTES = 512 << 20    # two halves of 256 MiB, each twice the L2 cache
 
 
 def load_peaks():
@@ -248,13 +249,14 @@ def run_multi_source(args, w, r):
 
 
 def parse_variant(v, w):
-    """'fp64' | 'exact' | 'bf16x3' | 'bf16' -> CDM with the workload's stabilisation;
-    'imex' -> Newmark IMEX (FP64); 'cons' -> CDM with the consistent cut mass (FP64);
+    """'fp64' | 'exact' | 'exact64' | 'bf16x3' | 'bf16' -> CDM with the workload's
+    stabilisation; 'imex[:exact64]' -> Newmark IMEX (its explicit part by the FP64 or the
+    FP64-grade tensor-core kernel); 'cons[:exact64]' -> CDM with the consistent cut mass;
     'ms:<precision>' -> CDM with mass scaling."""
-    if v == "imex":
-        return w.with_(scheme="imex", stab="none"), "fp64"
-    if v == "cons":
-        return w.with_(scheme="cdm_consistent"), "fp64"
+    if v.split(":")[0] == "imex":
+        return w.with_(scheme="imex", stab="none"), (v.split(":")[1] if ":" in v else "fp64")
+    if v.split(":")[0] == "cons":
+        return w.with_(scheme="cdm_consistent"), (v.split(":")[1] if ":" in v else "fp64")
     if v.startswith("ms:"):
         return w.with_(scheme="cdm", stab="mass_scaling"), v[3:]
     return w.with_(scheme="cdm" if w.scheme != "imex" else "cdm",
@@ -428,7 +430,10 @@ def run_ours(args, rank, world, local_rank):
                 dts[key] = w.dt_factor * dt_crit
         dt = dts[key]
         tile = None
-        if pv == "exact":
+        if pv == "exact" and args.tile_variant >= 0:
+            s.set_tile_variant(args.tile_variant)      # fixed tile shape (profiling)
+            tile = (args.tile_variant, [float("nan"), float("nan")])
+        elif pv == "exact":
             tile = s.autotune(reps=5)      # tile shape of the exact kernel for this problem
         s.set_dt(dt)
         s.set_initial()
@@ -548,7 +553,7 @@ def run_ours(args, rank, world, local_rank):
                        "n_dof": n_dof, "n_uncut": inf.n_uncut, "n_cut": inf.n_cut,
                        "n_cut_matrices": inf.n_cut_matrices,
                        "precision": best, "state": "fp64", "dt": dt,
-                       "l2": "flushed: 256 MiB device write before every timed step",
+                       "l2": "flushed before every timed step: 256 MiB device write, then 256 MiB read of another buffer (L2 left holding clean unrelated lines)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": rb["clocks"], "variants": variants_out}
@@ -571,11 +576,13 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precisions", default="fp64,exact")
+    ap.add_argument("--precisions", default="fp64,exact64,exact")
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="cells per axis of the plate (profiling)")
     ap.add_argument("--dt", type=float, default=0.0, help="fixed dt instead of 0.9 dt_crit (profiling)")
+    ap.add_argument("--tile-variant", type=int, default=-1,
+                    help="tile shape of the exact kernel instead of the autotuner's choice (profiling)")
     ap.add_argument("--run-steps", type=int, default=-1, help="steps of the accuracy run (-1: the workload's)")
     ap.add_argument("--run-time", type=float, default=0.0, help="simulated time of the accuracy run (overrides steps)")
     ap.add_argument("--sources", type=int, default=8,
