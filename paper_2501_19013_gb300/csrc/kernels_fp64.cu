@@ -443,6 +443,31 @@ cudaError_t launch_reduce_power(const double* partials, int nblocks, double* lam
   return cudaGetLastError();
 }
 
+// Reads `n` 16-byte words (an L2 eviction: the lines it brings in are clean); a thread writes
+// its xor to `sink` (a word of the flush buffer itself) only if it equals one arbitrary value,
+// so that the loads cannot be dropped and almost nothing is written.
+__global__ void l2_evict_read_kernel(const uint4* __restrict__ p, size_t n, unsigned* sink) {
+  uint32_t acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint4 v = p[i];
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x9E3779B9u) *sink = acc;
+}
+
+cudaError_t launch_l2_evict(void* buf, size_t bytes, cudaStream_t st) {
+  const size_t half = bytes / 2 / 16 * 16;
+  if (half == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(buf, 0x5a, half, st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  l2_evict_read_kernel<<<sms * 4, 512, 0, st>>>(reinterpret_cast<const uint4*>(static_cast<char*>(buf) + half), half / 16,
+                                              static_cast<unsigned*>(buf));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sample_now(const DevProblem& pb, const double* u, double* out, cudaStream_t st) {
   if (pb.n_obs_rows == 0) return cudaSuccess;
   sample_now_kernel<<<(pb.n_obs_rows + 127) / 128, 128, 0, st>>>(pb, u, out);
