@@ -1304,6 +1304,11 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
   d.hg_sn.clear();
   d.hg_frows.clear();
   d.hg_brows.clear();
+  d.hg_flpr.clear();
+  d.hg_blpr.clear();
+  // lanes per row of the row-parallel part: a group of short rows shares a warp among
+  // several rows (their loads in flight together), long rows get the whole warp
+  auto lanes_for = [](int64_t longest) { return longest <= 48 ? 4 : (longest <= 192 ? 8 : 32); };
   size_t q0 = 0;
   for (size_t c = 0; c + 1 < d.comp_ptr.size(); ++c) {
     size_t q1 = q0;
@@ -1312,6 +1317,7 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
     for (size_t q = q0; q < q1; ++q) hmax = std::max(hmax, d.sn_height[q]);
     for (int h = 0; h <= hmax; ++h) {
       bool any = false;
+      int64_t flong = 0, blong = 0;
       for (size_t q = q0; q < q1; ++q) {
         if (d.sn_height[q] != h) continue;
         any = true;
@@ -1319,9 +1325,13 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
         for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) {
           if (d.f_off_end[r] > L.Lp[r]) d.hg_frows.push_back((int32_t)r);
           if (L.Up[r + 1] > d.b_off_beg[r]) d.hg_brows.push_back((int32_t)r);
+          flong = std::max(flong, d.f_off_end[r] - L.Lp[r]);
+          blong = std::max(blong, L.Up[r + 1] - d.b_off_beg[r]);
         }
       }
       if (!any) continue;
+      d.hg_flpr.push_back(lanes_for(flong));
+      d.hg_blpr.push_back(lanes_for(blong));
       d.hg_sn_ptr.push_back((int32_t)d.hg_sn.size());
       d.hg_frow_ptr.push_back((int32_t)d.hg_frows.size());
       d.hg_brow_ptr.push_back((int32_t)d.hg_brows.size());

@@ -151,6 +151,7 @@ struct ImexData {
   std::vector<int32_t> hg_sn_ptr, hg_sn;        // per group: supernodes
   std::vector<int32_t> hg_frow_ptr, hg_frows;   // per group: rows with forward off-block entries
   std::vector<int32_t> hg_brow_ptr, hg_brows;   // per group: rows with backward off-block entries
+  std::vector<int32_t> hg_flpr, hg_blpr;        // per group: lanes per row (4, 8 or 32) by its longest row
 };
 // Build the partition and the pattern (dt-independent part).
 void imex_partition(const Setup& s, ImexData& d);

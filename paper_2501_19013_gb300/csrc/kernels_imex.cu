@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, Ime
 // order, one height group at a time (a supernode depends only on the supernodes below it in
 // the dissection tree, all in lower groups).  Per group: (1) every row with entries outside
 // its supernode subtracts them, w_r -= sum_j L_rj w_j (forward: columns j before the
-// supernode; backward, with L^T: rows j after it), one warp per row; (2) every supernode
+// supernode; backward, with L^T: rows j after it), 4, 8 or 32 lanes per row; (2) every supernode
 // (at most 32 rows) solves with its dense diagonal block of L by substitution, one warp per
 // supernode: the block is first copied to the warp's 32 x 32 shared-memory area with
 // independent coalesced loads, then the warp walks its columns (forward) or rows
@@ -71,17 +71,25 @@ __device__ __forceinline__ void block_solve(const ImexDev& im, int g0, int g1, d
   double* const S = scratch + warp * kSnMax * kSnMax;
   for (int gi = 0; gi < g1 - g0; ++gi) {
     const int g = FWD ? g0 + gi : g1 - 1 - gi;
-    const int32_t* rows = FWD ? im.hg_frows : im.hg_brows;
+    const int4* __restrict__ desc = FWD ? im.hg_fdesc : im.hg_bdesc;
     const int q0 = FWD ? im.hg_frow_ptr[g] : im.hg_brow_ptr[g];
     const int q1 = FWD ? im.hg_frow_ptr[g + 1] : im.hg_brow_ptr[g + 1];
-    for (int q = q0 + warp; q < q1; q += nwarps) {
-      const int r = rows[q];
-      const int64_t a0 = FWD ? im.Lp[r] : im.b_off_beg[r];
-      const int64_t a1 = FWD ? im.f_off_end[r] : im.Up[r + 1];
+    // lpr lanes per row, 32 / lpr rows per warp at a time (the host picks lpr by the
+    // group's longest row); a row's entries are strided over its lanes, four loads in flight
+    const int lpr = FWD ? im.hg_flpr[g] : im.hg_blpr[g];
+    const int rpw = 32 / lpr, sub = lane & (lpr - 1), slot = lane / lpr;
+    for (int qb = q0 + warp * rpw; qb < q1; qb += nwarps * rpw) {
+      const int q = qb + slot;
       double acc = 0.0;
-      for (int64_t p = a0 + lane; p < a1; p += 32) acc = fma(X[p], w[I[p]], acc);
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) w[r] -= acc;
+      int r = -1;
+      if (q < q1) {
+        const int4 dq = desc[q];
+        r = dq.x;
+#pragma unroll 4
+        for (int p = dq.y + sub; p < dq.z; p += lpr) acc = fma(X[p], w[I[p]], acc);
+      }
+      for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lpr);
+      if (sub == 0 && r >= 0) w[r] -= acc;
     }
     __syncthreads();
     for (int q = im.hg_sn_ptr[g] + warp; q < im.hg_sn_ptr[g + 1]; q += nwarps) {
@@ -116,7 +124,7 @@ extern __shared__ double imex_smem[];
 constexpr int kImexThreads = 512;
 constexpr int kImexScratch = kImexThreads / 32 * kSnMax * kSnMax;
 
-__global__ void __launch_bounds__(kImexThreads) imex_solve_kernel(DevProblem pb, ImexDev im, double* __restrict__ out,
+__global__ void __launch_bounds__(kImexThreads, 1) imex_solve_kernel(DevProblem pb, ImexDev im, double* __restrict__ out,
                                                                   int in_smem) {
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(kImexThreads) imex_solve_kernel(DevProblem pb,
 // iteration of the consistent-mass CDM (S = M^cc there): one CTA per component; the right-
 // hand side is b[r] = in[c_dof[perm[r]]] * scal, the solution of L w = b (forward) or of
 // L^T w = b (backward) is written to out[c_dof[perm[r]]].
-__global__ void __launch_bounds__(kImexThreads, 1) imex_tri_kernel(ImexDev im, const double* __restrict__ in,
+__global__ void __launch_bounds__(kImexThreads) imex_tri_kernel(ImexDev im, const double* __restrict__ in,
                                                         const double* __restrict__ scal,
                                                         double* __restrict__ out, int backward, int in_smem) {
   const int b = blockIdx.x;
