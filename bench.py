@@ -473,6 +473,7 @@ def run_ours(args, rank, world, local_rank):
                              clocks=clk, run_s=run_s, u_end=u_end, series=series, solver=s, wall=t_wall, dt=dt,
                              run_steps=run_steps, scheme=wv.scheme, stab=wv.stab,
                              tile=None if tile is None else {"variant": tile[0], "cells": list(s.info().tile),
+                                                              "ctas_per_sm_cap": int(s.info().tc_ctas_per_sm),
                                                               "autotune_ms_per_apply": [float(x) for x in tile[1]]})
     accuracy_against_fp64(results)
     # headline: fastest variant that reaches rel-L2 <= 1e-4 against FP64

@@ -155,6 +155,9 @@ typedef struct {
     size_t shared_device_bytes; /* part of device_bytes held jointly with the handle's
                                  clones (or its source): geometry, cut-cell and
                                  reference matrices; freed with the last of them          */
+    int32_t tc_ctas_per_sm;   /* cap on the exact kernel's resident CTAs per SM (0: as
+                                 many as fit), set by ibfem_autotune                     */
+    int32_t autotune_cached;  /* 1 if the last ibfem_autotune reused a cached choice     */
 } ibfem_info_t;
 
 /* ---- lifetime -------------------------------------------------------------------- */
@@ -311,9 +314,14 @@ int ibfem_get_element_mass(ibfem_t* h, int64_t cell, double* M);
  * of one MMA with the halo'd tile (2D: 8x8 cells for n_loc >= 32, else 15x7; 3D: 4x4x4),
  * variant 1 is smaller (2D: 5x5 or 7x7; 3D: 3x3x3): more tiles for small problems and, in
  * 3D, less shared memory per CTA.  ibfem_set_tile_variant picks one; ibfem_autotune times
- * reps operator applications with each (the state is untouched), keeps the faster and
- * returns its index and both times (ms per application) in ms[2].  The FP64 path and the
- * BF16 schemes have variant 0 only (ibfem_autotune then returns 0 and zero times).
+ * reps operator applications (the state is untouched) for each tile shape and each cap on
+ * the persistent launch's resident CTAs per SM (as many as fit, or one), keeps the fastest
+ * pair, and returns its tile shape and the best time of each shape (ms per application) in
+ * ms[2].  The choice is cached per (device, dim, p, ncomp, log2 of the cell count) for the
+ * life of the process: a later handle of the same class takes it without timing
+ * (ibfem_info reports the cap and whether the cache answered).  The FP64 path and the BF16
+ * schemes have variant 0 only (ibfem_autotune then returns 0 and zero times); the
+ * FP64-grade path has one tile shape (returned, zero times).
  * Results of the two variants agree within the exact scheme's accuracy (the digit
  * exponent is per tile), not bitwise.  This is a part of this library; the paper has no
  * counterpart.  Errors: ARG, STATE (batch member), CUDA.                                  */

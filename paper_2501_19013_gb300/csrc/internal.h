@@ -109,6 +109,8 @@ struct ImexDev {
   const int32_t *hg_sn_ptr, *hg_sn;
   const int32_t *hg_frow_ptr, *hg_frows;
   const int32_t *hg_brow_ptr, *hg_brows;
+  const int32_t *hg_flpr, *hg_blpr;   // per group: lanes per row of the row-parallel part
+  const int4 *hg_fdesc, *hg_bdesc;    // per listed row: {row, first off-block entry, end, 0}
   const int64_t* perm;       // permuted row -> c index
   const int64_t* c_dof;      // c index -> lattice DOF
   double* vc;
@@ -153,9 +155,10 @@ int op_fp64_blocks(const DevProblem& pb);
 cudaError_t launch_l2_evict(void* buf, size_t bytes, cudaStream_t st);
 // Launchers (kernels_tc.cu)
 // scheme: 0 exact digit slices, 1 bf16 hi/lo three-pass, 2 bf16 one pass
-// variant: tile shape (0 full MMA tile, 1 small tile; 1 only with scheme 0)
+// variant: tile shape (0 full MMA tile, 1 small tile; 1 only with scheme 0); ctas_per_sm:
+// cap on the resident CTAs per SM of the persistent launch (0: as many as fit)
 cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme, int variant,
-                         cudaStream_t st);
+                         cudaStream_t st, int ctas_per_sm = 0);
 // Batched launch (exact scheme, CDM): every member advances one step; members[m] owns the
 // global tiles [tile_start[m], tile_start[m + 1]).
 cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, int variant, const BatchMember* members,

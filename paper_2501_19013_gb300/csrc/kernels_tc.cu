@@ -918,13 +918,20 @@ static int tc_configure(KernelT kernel, size_t smem_launch, int tmem_max) {
 }
 
 template <int D, int P, int N, int S, int T>
-static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* out, int mode, cudaStream_t st) {
+static cudaError_t launch_tc_t(const DevProblem& pb, const double* u, double* out, int mode, int ctas_per_sm,
+                               cudaStream_t st) {
   using C = TcCfg<D, P, N, T>;
   // thread-safe one-time configuration (function-local static initialisation)
   static const int resident = tc_configure(op_tc_kernel<D, P, N, S, false, T>, C::SMEM_LAUNCH, C::CTA_TMEM_MAX);
   if (resident == 0) return cudaErrorInvalidConfiguration;
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }();
   int tiles = pb.tc_tiles[0] * pb.tc_tiles[1] * pb.tc_tiles[2];
-  int blocks = std::min(tiles, resident);
+  int blocks = std::min(tiles, ctas_per_sm > 0 ? std::min(resident, ctas_per_sm * sms) : resident);
   op_tc_kernel<D, P, N, S, false, T><<<blocks, 256, C::SMEM_LAUNCH, st>>>(pb, u, out, mode, nullptr, nullptr, 0, 0,
                                                                          nullptr);
   return cudaGetLastError();
@@ -961,14 +968,14 @@ cudaError_t launch_op_tc_batch(int dim, int p, int ncomp, int variant, const Bat
 // the small tile (variant 1) exists for the exact scheme, which is the one the batch and
 // the serving loop run
 cudaError_t launch_op_tc(const DevProblem& pb, const double* u, double* out, int mode, int scheme, int variant,
-                         cudaStream_t st) {
+                         cudaStream_t st, int ctas_per_sm) {
 #define X(D, P, N)                                                                 \
   if (pb.dim == D && pb.p == P && pb.ncomp == N) {                                 \
-    if (scheme == 0 && variant == 1) return launch_tc_t<D, P, N, 0, 1>(pb, u, out, mode, st); \
+    if (scheme == 0 && variant == 1) return launch_tc_t<D, P, N, 0, 1>(pb, u, out, mode, ctas_per_sm, st); \
     if (variant != 0) return cudaErrorInvalidValue;                                \
-    if (scheme == 0) return launch_tc_t<D, P, N, 0, 0>(pb, u, out, mode, st);      \
-    if (scheme == 1) return launch_tc_t<D, P, N, 1, 0>(pb, u, out, mode, st);      \
-    return launch_tc_t<D, P, N, 2, 0>(pb, u, out, mode, st);                       \
+    if (scheme == 0) return launch_tc_t<D, P, N, 0, 0>(pb, u, out, mode, ctas_per_sm, st);      \
+    if (scheme == 1) return launch_tc_t<D, P, N, 1, 0>(pb, u, out, mode, ctas_per_sm, st);      \
+    return launch_tc_t<D, P, N, 2, 0>(pb, u, out, mode, ctas_per_sm, st);                       \
   }
   IBFEM_TC_SHAPES(X)
 #undef X

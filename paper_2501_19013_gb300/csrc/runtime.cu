@@ -8,7 +8,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -497,6 +500,23 @@ void Handle::imex_upload_factor() {
     D.hg_frows = upload(I.hg_frows);
     D.hg_brow_ptr = upload(I.hg_brow_ptr);
     D.hg_brows = upload(I.hg_brows);
+    D.hg_flpr = upload(I.hg_flpr);
+    D.hg_blpr = upload(I.hg_blpr);
+    // one 16-byte descriptor per listed row (its entry range), so that a row costs one load
+    // before its entries (the pattern does not depend on dt)
+    if (nnz > (size_t)INT32_MAX) throw std::runtime_error("IMEX factor too large for 32-bit entry offsets");
+    auto desc = [&](const std::vector<int32_t>& rows, bool fwd) {
+      std::vector<int32_t> v(4 * std::max<size_t>(rows.size(), 1), 0);
+      for (size_t q = 0; q < rows.size(); ++q) {
+        const int32_t r = rows[q];
+        v[4 * q] = r;
+        v[4 * q + 1] = (int32_t)(fwd ? L.Lp[r] : I.b_off_beg[r]);
+        v[4 * q + 2] = (int32_t)(fwd ? I.f_off_end[r] : L.Up[r + 1]);
+      }
+      return v;
+    };
+    D.hg_fdesc = reinterpret_cast<const int4*>(upload(desc(I.hg_frows, true)));
+    D.hg_bdesc = reinterpret_cast<const int4*>(upload(desc(I.hg_brows, false)));
     imex_nnz_alloc = nnz;
   }
   auto cp = [&](const void* dst, const void* src, size_t bytes) {
@@ -580,7 +600,7 @@ void Handle::enqueue_step(int cur) {
     slot_name[1] = tc_scheme() == 0 ? "op_tc_exact_fused_cdm" : (tc_scheme() == 1 ? "op_tc_bf16x3_fused_cdm" : "op_tc_bf16_fused_cdm");
     if (timing) step_first_ev.push_back(ev_used);
     timed_begin(1);
-    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_scheme(), tc_variant, stream), "op_tc");
+    check(launch_op_tc(dev, U[cur], U[1 - cur], kModeCDM, tc_scheme(), tc_variant, stream, tc_ctas), "op_tc");
     timed_end();
     if (timing) step_last_ev.push_back(ev_used - 1);
     return;
@@ -900,6 +920,8 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
   out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes + out->shared_device_bytes;
   out->n_cut_matrices = s.n_cut_mat;
   out->tile_variant = h->tc_variant;
+  out->tc_ctas_per_sm = h->tc_ctas;
+  out->autotune_cached = h->tune_cached ? 1 : 0;
   for (int k = 0; k < 3; ++k) out->tile[k] = h->tc_tile[k];
   return IBFEM_OK;
 }
@@ -1308,7 +1330,8 @@ int ibfem_apply_operator(ibfem_t* h, const double* x, double* y) {
     check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
     check(launch_op_tc64(h->dev, h->W, h->scratch, kModeApply, h->stream), "apply_tc64");
   } else if (h->opt.precision != IBFEM_FP64) {
-    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_scheme(), h->tc_variant, h->stream), "apply_tc");
+    check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, h->tc_scheme(), h->tc_variant, h->stream, h->tc_ctas),
+          "apply_tc");
   } else {
     check(launch_cut_apply_fp64(h->dev, in, false, h->stream), "cut_apply");
     check(launch_op_fp64(h->dev, in, h->scratch, kModeApply, nullptr, h->stream), "apply");
@@ -1335,6 +1358,21 @@ int ibfem_set_tile_variant(ibfem_t* h, int variant) {
   IBFEM_CATCH
 }
 
+}  // extern "C"
+
+namespace {
+// Choices of the exact kernel's autotuner, per (device, dim, p, ncomp, log2 of the cell
+// count): later handles of the same class of problem reuse them without timing.
+struct TuneChoice {
+  int variant, ctas;
+  double ms[2];
+};
+std::mutex g_tune_mutex;
+std::map<std::array<int, 5>, TuneChoice> g_tune_cache;
+}  // namespace
+
+extern "C" {
+
 int ibfem_autotune(ibfem_t* h, int reps, int* variant, double* ms) {
   int rc = require_device(h);
   if (rc) return rc;
@@ -1342,29 +1380,66 @@ int ibfem_autotune(ibfem_t* h, int reps, int* variant, double* ms) {
   IBFEM_TRY
   double t[2] = {0.0, 0.0};
   int best = 0;
+  h->tune_cached = false;
   if (h->opt.precision != IBFEM_FP64 && h->tc_scheme() == 0) {
-    // time reps operator applications (the step's kernel in apply mode, on work vectors:
-    // the state is untouched) with each tile shape, after two untimed ones
-    cudaEvent_t e0, e1;
-    check(cudaEventCreate(&e0), "event");
-    check(cudaEventCreate(&e1), "event");
-    for (int v = 0; v < 2; ++v) {
-      h->set_tc_variant(v);
-      for (int i = 0; i < 2; ++i)
-        check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, 0, v, h->stream), "autotune");
-      check(cudaEventRecord(e0, h->stream), "event");
-      for (int i = 0; i < reps; ++i)
-        check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, 0, v, h->stream), "autotune");
-      check(cudaEventRecord(e1, h->stream), "event");
-      check(cudaEventSynchronize(e1), "event");
-      float f = 0.f;
-      check(cudaEventElapsedTime(&f, e0, e1), "event");
-      t[v] = f / reps;
+    const Setup& s = h->setup;
+    int lg = 0;
+    for (int64_t c = s.n_elem; c > 1; c >>= 1) ++lg;
+    const std::array<int, 5> key = {h->opt.device, s.dim, s.p, s.ncomp, lg};
+    bool hit = false;
+    TuneChoice ch{};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        ch = it->second;
+        hit = true;
+      }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    best = t[1] < t[0] ? 1 : 0;
-    h->set_tc_variant(best);
+    if (!hit) {
+      // time reps operator applications (the step's kernel in apply mode, on work vectors:
+      // the state is untouched) for each tile shape and each cap on the resident CTAs per
+      // SM (as many as fit, one), after two untimed ones
+      cudaEvent_t e0, e1;
+      check(cudaEventCreate(&e0), "event");
+      check(cudaEventCreate(&e1), "event");
+      double best_ms = 1e300;
+      ch.ms[0] = ch.ms[1] = 1e300;
+      for (int v = 0; v < 2; ++v) {
+        h->set_tc_variant(v);
+        for (int c : {0, 1}) {
+          for (int i = 0; i < 2; ++i)
+            check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, 0, v, h->stream, c), "autotune");
+          check(cudaEventRecord(e0, h->stream), "event");
+          for (int i = 0; i < reps; ++i)
+            check(launch_op_tc(h->dev, h->W, h->scratch, kModeApply, 0, v, h->stream, c), "autotune");
+          check(cudaEventRecord(e1, h->stream), "event");
+          check(cudaEventSynchronize(e1), "event");
+          float f = 0.f;
+          check(cudaEventElapsedTime(&f, e0, e1), "event");
+          const double m = (double)f / reps;
+          ch.ms[v] = std::min(ch.ms[v], m);
+          if (m < best_ms) {
+            best_ms = m;
+            ch.variant = v;
+            ch.ctas = c;
+          }
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_cache[key] = ch;
+    }
+    h->set_tc_variant(ch.variant);
+    if (h->tc_ctas != ch.ctas) {
+      h->tc_ctas = ch.ctas;
+      h->invalidate_graphs();
+    }
+    h->tune_cached = hit;
+    best = ch.variant;
+    t[0] = ch.ms[0];
+    t[1] = ch.ms[1];
   } else if (h->opt.precision == IBFEM_EXACT64_TC) {
     best = h->tc_variant;   // one tile shape
   }

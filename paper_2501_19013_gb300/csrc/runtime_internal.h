@@ -49,6 +49,8 @@ struct Handle {
   float* d_minv32 = nullptr;
   int tc_tile[3] = {1, 1, 1};
   int tc_variant = 0;          // tile shape of the tensor-core kernel (0 full, 1 small)
+  int tc_ctas = 0;             // resident CTAs per SM of the exact kernel (0: as many as fit)
+  bool tune_cached = false;    // the last ibfem_autotune took its choice from the cache
   void build_tc_tiles();
   void upload_tc_sources();
   void set_tc_variant(int v);

@@ -65,7 +65,8 @@ class Info(C.Structure):
                 ("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double),
                 ("lambda_ref", C.c_double), ("device_bytes", C.c_size_t),
                 ("n_cut_matrices", C.c_int64), ("tile_variant", C.c_int32), ("tile", C.c_int32 * 3),
-                ("shared_device_bytes", C.c_size_t)]
+                ("shared_device_bytes", C.c_size_t), ("tc_ctas_per_sm", C.c_int32),
+                ("autotune_cached", C.c_int32)]
 
 
 _lib = None

@@ -101,3 +101,31 @@ def test_autotune_picks_the_faster_variant():
     assert ms[v] == min(ms)
     assert s.info().tile_variant == v
     s.close()
+
+
+def test_autotune_cache_and_cta_cap_keep_the_arithmetic():
+    """The tuner's choice (tile shape, cap on resident CTAs per SM) is cached per class of
+    problem: a second handle of the same shape takes it without timing.  The cap only moves
+    tiles between CTAs, so a run under it is bitwise the run of the same tile shape without."""
+    from paper_2501_19013_gb300 import workloads as W
+    w = W.plate_holes_elastic(n=48, p=4, count=3, steps=40)
+    a = gpu_solver(w, precision="exact")
+    va, _ = a.autotune(reps=3)
+    b = gpu_solver(w, precision="exact")
+    vb, _ = b.autotune(reps=3)
+    ia, ib_ = a.info(), b.info()
+    assert vb == va and ib_.tile_variant == va and ib_.tc_ctas_per_sm == ia.tc_ctas_per_sm
+    assert ib_.autotune_cached == 1
+    c = gpu_solver(w, precision="exact")
+    c.set_tile_variant(va)             # same tile shape, no cap on the CTAs
+    assert c.info().tc_ctas_per_sm == 0
+    out = []
+    for s in (b, c):
+        s.set_dt(2e-4)
+        s.set_initial()
+        s.step(w.steps)
+        s.sync()
+        out.append(s.get_state()[0])
+    assert np.array_equal(out[0], out[1])
+    for s in (a, b, c):
+        s.close()
