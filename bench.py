@@ -323,11 +323,11 @@ def aggregate_replicas(step_ms, n_dof, world, device=None):
     return step_ms, n_dof / (step_ms * 1e-3)
 
 
-# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, cold cache)
-# of the current kernel code on the benchmark workload; to be re-taken whenever the kernel
-# changes
-MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.368128e6 + 2.093312e6,
-                    ("op_tc_exact_fused_cdm", "porous_voxel_64^3_p3", 1): 328.21e6 + 37.94e6}
+# DRAM bytes of one CDM launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, cold
+# cache) of the current kernel code on the benchmark workload (profiles/ gives the command);
+# to be re-taken whenever the kernel changes
+MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.364288e6 + 2.308608e6,
+                    ("op_tc_exact64_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 51.207424e6 + 0.105984e6}
 
 # arithmetic of each variant's element operator (the state and the update are FP64 in all)
 DTYPES = {"fp64": "f64",
@@ -390,7 +390,7 @@ def roofline(prec, kname, kms, inf, w, peaks, r):
     achieved = byts / (kms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     variant = r["tile"]["variant"] if r.get("tile") else 0
-    traffic = MEASURED_TRAFFIC.get((kname, w.name, variant)) if prec == "exact" else None
+    traffic = MEASURED_TRAFFIC.get((kname, w.name, variant)) if prec in ("exact", "exact64") else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": kname,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
