@@ -1296,48 +1296,57 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
         DT[j * w + i] = v;
       }
   }
-  // height groups per component (components own contiguous runs of supernodes)
-  d.comp_hg.assign(1, 0);
-  d.hg_sn_ptr.assign(1, 0);
-  d.hg_frow_ptr.assign(1, 0);
-  d.hg_brow_ptr.assign(1, 0);
-  d.hg_sn.clear();
-  d.hg_frows.clear();
-  d.hg_brows.clear();
-  d.hg_flpr.clear();
-  d.hg_blpr.clear();
-  // lanes per row of the row-parallel part: a group of short rows shares a warp among
-  // several rows (their loads in flight together), long rows get the whole warp
-  auto lanes_for = [](int64_t longest) { return longest <= 48 ? 4 : (longest <= 192 ? 8 : 32); };
-  size_t q0 = 0;
-  for (size_t c = 0; c + 1 < d.comp_ptr.size(); ++c) {
-    size_t q1 = q0;
-    while (q1 < nsn && d.sn_start[q1] < d.comp_ptr[c + 1]) ++q1;
-    int hmax = -1;
-    for (size_t q = q0; q < q1; ++q) hmax = std::max(hmax, d.sn_height[q]);
+  // supernodes by height of the dissection tree over all components (the GPU solves every
+  // supernode of one height per launch)
+  int hmax = -1;
+  for (size_t q = 0; q < nsn; ++q) hmax = std::max(hmax, d.sn_height[q]);
+  d.gh_sn_ptr.assign(1, 0);
+  d.gh_sn.clear();
+  for (int h = 0; h <= hmax; ++h) {
+    for (size_t q = 0; q < nsn; ++q)
+      if (d.sn_height[q] == h) d.gh_sn.push_back((int32_t)q);
+    d.gh_sn_ptr.push_back((int32_t)d.gh_sn.size());
+  }
+  // work split of the off-block sums, per direction: a supernode whose rows hold E entries
+  // gets g = ceil(E / kImexCtaEntries) CTAs (at most kImexMaxSplit), each taking the same
+  // fraction of every row; lanes per row 4, 8 or 32 by the longest share of a row (short
+  // rows share a warp, their loads in flight together); partial sums of split supernodes at
+  // sn_pbase (32 per CTA); the CTAs of each height listed in height order
+  for (int dir = 0; dir < 2; ++dir) {
+    ImexSplit& sp = dir == 0 ? d.fsplit : d.bsplit;
+    sp.g.assign(nsn, 1);
+    sp.lpr.assign(nsn, 4);
+    sp.pbase.assign(nsn, 0);
+    int64_t parts = 0;
+    for (size_t q = 0; q < nsn; ++q) {
+      int64_t tot = 0, lng = 0;
+      for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) {
+        const int64_t len = dir == 0 ? d.f_off_end[r] - L.Lp[r] : L.Up[r + 1] - d.b_off_beg[r];
+        tot += len;
+        lng = std::max(lng, len);
+      }
+      const int64_t g = std::min<int64_t>(kImexMaxSplit, std::max<int64_t>(1, (tot + kImexCtaEntries - 1) / kImexCtaEntries));
+      const int64_t share = (lng + g - 1) / g;
+      sp.g[q] = (int32_t)g;
+      sp.lpr[q] = share <= 48 ? 4 : (share <= 192 ? 8 : 32);
+      if (g > 1) {
+        sp.pbase[q] = parts;
+        parts += g * 32;
+      }
+    }
+    sp.n_parts = parts;
+    sp.cta.clear();
+    sp.cta_ptr.assign(1, 0);
     for (int h = 0; h <= hmax; ++h) {
-      bool any = false;
-      int64_t flong = 0, blong = 0;
-      for (size_t q = q0; q < q1; ++q) {
-        if (d.sn_height[q] != h) continue;
-        any = true;
-        d.hg_sn.push_back((int32_t)q);
-        for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) {
-          if (d.f_off_end[r] > L.Lp[r]) d.hg_frows.push_back((int32_t)r);
-          if (L.Up[r + 1] > d.b_off_beg[r]) d.hg_brows.push_back((int32_t)r);
-          flong = std::max(flong, d.f_off_end[r] - L.Lp[r]);
-          blong = std::max(blong, L.Up[r + 1] - d.b_off_beg[r]);
+      for (int32_t k = d.gh_sn_ptr[h]; k < d.gh_sn_ptr[h + 1]; ++k) {
+        const int32_t q = d.gh_sn[k];
+        for (int32_t c = 0; c < sp.g[q]; ++c) {
+          sp.cta.push_back(q);
+          sp.cta.push_back(c);
         }
       }
-      if (!any) continue;
-      d.hg_flpr.push_back(lanes_for(flong));
-      d.hg_blpr.push_back(lanes_for(blong));
-      d.hg_sn_ptr.push_back((int32_t)d.hg_sn.size());
-      d.hg_frow_ptr.push_back((int32_t)d.hg_frows.size());
-      d.hg_brow_ptr.push_back((int32_t)d.hg_brows.size());
+      sp.cta_ptr.push_back((int32_t)(sp.cta.size() / 2));
     }
-    d.comp_hg.push_back((int32_t)d.hg_sn_ptr.size() - 1);
-    q0 = q1;
   }
   return true;
 }

@@ -116,6 +116,21 @@ bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vecto
 // the consistent M^cc and K^cc on it, and the Cholesky factor of S = M^cc + beta dt^2 K^cc
 // in a fill-reducing order (connected components, then geometric nested dissection), with
 // the supernodes of that order for the block triangular solves.
+// Entries of off-block sums per CTA of the GPU block solve, and the most CTAs one
+// supernode's sums are split over.
+constexpr int64_t kImexCtaEntries = 2048;
+constexpr int64_t kImexMaxSplit = 256;
+
+// Split of one direction's off-block sums (forward: L y = b; backward: L^T x = y).
+struct ImexSplit {
+  std::vector<int32_t> g;        // per supernode: CTAs
+  std::vector<int32_t> lpr;      // per supernode: lanes per row (4, 8 or 32)
+  std::vector<int64_t> pbase;    // per supernode split over g > 1 CTAs: first partial sum
+  int64_t n_parts = 0;           // partial sums of all split supernodes
+  std::vector<int32_t> cta;      // per CTA of the level launches: {supernode, share}
+  std::vector<int32_t> cta_ptr;  // per height: first CTA (heights + 1 entries)
+};
+
 struct ImexData {
   int64_t n_c = 0;
   std::vector<int64_t> c_dof;          // c index -> lattice DOF (lattice order)
@@ -141,17 +156,14 @@ struct ImexData {
   // block solve data (rebuilt with the factor): per supernode its dense diagonal block of L
   // (w x w, row-major, zeros above the diagonal, 1 / L_jj on it) and its transpose, at
   // sn_doff; per row the end of its off-block part in the CSR of L (forward) and the start of
-  // its off-block part in the CSR of L^T (backward); per component its height groups, in
-  // increasing height, each a list of supernodes and a list of the rows that have off-block
-  // entries (forward / backward)
+  // its off-block part in the CSR of L^T (backward)
   std::vector<int64_t> sn_doff;
   std::vector<double> sn_D, sn_DT;
   std::vector<int64_t> f_off_end, b_off_beg;
-  std::vector<int32_t> comp_hg;                 // per component: range of height groups
-  std::vector<int32_t> hg_sn_ptr, hg_sn;        // per group: supernodes
-  std::vector<int32_t> hg_frow_ptr, hg_frows;   // per group: rows with forward off-block entries
-  std::vector<int32_t> hg_brow_ptr, hg_brows;   // per group: rows with backward off-block entries
-  std::vector<int32_t> hg_flpr, hg_blpr;        // per group: lanes per row (4, 8 or 32) by its longest row
+  // the supernodes grouped by height over all components (the GPU solves one height of every
+  // component per launch), and the split of their off-block sums over CTAs per direction
+  std::vector<int32_t> gh_sn_ptr, gh_sn;
+  ImexSplit fsplit, bsplit;
 };
 // Build the partition and the pattern (dt-independent part).
 void imex_partition(const Setup& s, ImexData& d);

@@ -78,13 +78,20 @@ struct BatchCtl {
 };
 
 // Device view of the IMEX partition and factor (kernels_imex.cu).
+// One direction's CTAs of the block solve (host-side ImexSplit on the device).
+struct ImexSplitDev {
+  const int2* cta;           // per CTA: {supernode, share c of g}
+  const int32_t* g;          // per supernode: CTAs its off-block sums are split over
+  const int32_t* lpr;        // per supernode: lanes per row
+  const int64_t* pbase;      // per split supernode: first partial sum (32 per CTA)
+  const int32_t* cta_ptr_host;   // host array: heights + 1 offsets into cta
+};
+
 struct ImexDev {
   int n_cells;               // cells touching the c-set
   const int64_t* cells;
   double* Y;                 // n_cells * n_loc products K^e x_e
-  int n_comp;                // connected components = CTAs of the solve
-  const int32_t* comp_ptr;   // permuted-row ranges of the components
-  int max_comp;              // rows of the largest component (its vector in shared memory)
+  int64_t n_rows;            // c-DOFs (rows of S, permuted order)
   const int64_t* g_ptr;      // residual gather per permuted row
   const int32_t* g_idx;
   const double* Fc;          // spatial load on the c-DOFs (permuted rows), or null
@@ -93,24 +100,23 @@ struct ImexDev {
   const double* Lx;
   const int64_t *Up, *Ui;    // L^T by rows, diagonal first
   const double* Ux;
-  // block triangular solves: supernodes (contiguous permuted rows) with the inverse D of
-  // their dense diagonal block of L (row-major w x w at sn_doff) and its transpose DT; per
-  // row the end of its off-block entries in L and their start in L^T; per component its
-  // height groups, each a list of supernodes and the rows with forward / backward off-block
-  // entries
+  // block triangular solves: supernodes (contiguous permuted rows of at most 32) with the
+  // dense diagonal block of L (row-major w x w at sn_doff, 1 / L_jj on the diagonal) and
+  // its transpose DT; per row the range of its off-block entries in L (forward) and in L^T
+  // (backward); per direction the CTAs of each height of the dissection tree (one launch
+  // per height, the ranges on the host), the split of each supernode's off-block sums over
+  // its CTAs, their partial sums and one arrival counter per supernode
   const int64_t* sn_start;
   const int32_t* sn_w;
   const int64_t* sn_doff;
   const double* D;
   const double* DT;
-  const int64_t* f_off_end;
-  const int64_t* b_off_beg;
-  const int32_t* comp_hg;
-  const int32_t *hg_sn_ptr, *hg_sn;
-  const int32_t *hg_frow_ptr, *hg_frows;
-  const int32_t *hg_brow_ptr, *hg_brows;
-  const int32_t *hg_flpr, *hg_blpr;   // per group: lanes per row of the row-parallel part
-  const int4 *hg_fdesc, *hg_bdesc;    // per listed row: {row, first off-block entry, end, 0}
+  const int2* row_fdesc;     // {Lp[r], end of the off-block entries of row r}
+  const int2* row_bdesc;     // {start of the off-block entries of row r of L^T, Up[r + 1]}
+  ImexSplitDev fs, bs;       // forward, backward
+  double* part;
+  unsigned int* cnt;         // zero between launches (the last CTA of a supernode resets it)
+  int n_heights;
   const int64_t* perm;       // permuted row -> c index
   const int64_t* c_dof;      // c index -> lattice DOF
   double* vc;

@@ -5,13 +5,15 @@
 // (and Psi'_pred^c) into the new state buffer:
 //   * imex_cell_apply : y_e = K^e x_e for every cell touching a c-DOF (one warp per cell,
 //                       FP64), x = [Psi_{k+1}^d ; Psi_pred^c];
-//   * imex_solve      : one CTA per connected component of the c-set: the residual
-//                       r = F^c_{k+1} - K^c Psi_pred gathered in a fixed order, the
-//                       forward and backward solves with the host Cholesky factor of
-//                       S = M^cc + beta dt^2 K^cc by supernode blocks, and the Newmark correction
+//   * imex_solve      : the residual r = F^c_{k+1} - K^c Psi_pred gathered in a fixed
+//                       order, the forward and backward solves with the host Cholesky
+//                       factor of S = M^cc + beta dt^2 K^cc by supernode blocks (one launch
+//                       per height of the dissection tree), and the Newmark correction
 //                       Psi''^c = S^{-1} r, Psi'^c = Psi'_pred^c + gamma dt Psi''^c,
-//                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c.  The last CTA advances the
-//                       step counter.
+//                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c, which advances the step
+//                       counter.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace ibfem {
@@ -51,164 +53,174 @@ __global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, Ime
   }
 }
 
-// Block triangular solve of one component over the supernodes of its nested-dissection
-// order, one height group at a time (a supernode depends only on the supernodes below it in
-// the dissection tree, all in lower groups).  Per group: (1) every row with entries outside
-// its supernode subtracts them, w_r -= sum_j L_rj w_j (forward: columns j before the
-// supernode; backward, with L^T: rows j after it), 4, 8 or 32 lanes per row; (2) every supernode
-// (at most 32 rows) solves with its dense diagonal block of L by substitution, one warp per
-// supernode: the block is first copied to the warp's 32 x 32 shared-memory area with
-// independent coalesced loads, then the warp walks its columns (forward) or rows
-// (backward) while the lanes update the other rows; a block barrier after each part.
-// FWD: L y = b; else L^T x = y.
-constexpr int kSnMax = 32;   // rows of a supernode (the host splits longer runs)
+// Block triangular solves over the supernodes of the nested-dissection order (each leaf
+// block and each separator, a contiguous run of at most 32 rows, depends only on the
+// supernodes below it in the dissection tree).  One launch per tree height, over every
+// component: the launches of lower (forward) or higher (backward) heights have completed,
+// so every row a supernode reads is final.  For each supernode:
+//   (1) its rows' entries outside the diagonal block (forward: columns before it; backward,
+//       rows of L^T: columns after it) are summed by g CTAs, each taking the same fraction
+//       of every row, with 4, 8 or 32 lanes on a row (g and the lanes fixed on the host by
+//       the entry counts: the separators near the top of the tree reach far back and get
+//       many CTAs);
+//   (2) with g > 1 each CTA stores its 32 partial sums and counts itself in; the last CTA
+//       to arrive adds the partials in share order (the sum does not depend on the arrival
+//       order) and resets the counter;
+//   (3) that CTA solves t_i = w_i - sum_i with the dense diagonal block by substitution in
+//       shared memory (walking its columns forward, its rows backward, lanes over the other
+//       rows) and writes the block's rows back.
+// FWD: L y = b; else L^T x = y.  No CTA waits on another.
+constexpr int kSnMax = 32;          // rows of a supernode (the host splits longer runs)
+constexpr int kLevelThreads = 256;  // threads of a level CTA
 
 template <bool FWD>
-__device__ __forceinline__ void block_solve(const ImexDev& im, int g0, int g1, double* w, double* scratch,
-                                            int lane, int warp, int nwarps) {
+__global__ void __launch_bounds__(kLevelThreads) imex_level_kernel(ImexDev im, int c0) {
+  __shared__ double S[kSnMax * kSnMax];
+  __shared__ double T[kSnMax];
+  __shared__ int last;
+  const ImexSplitDev& sp = FWD ? im.fs : im.bs;
+  const int2 task = sp.cta[c0 + blockIdx.x];
+  const int sn = task.x, c = task.y;
+  const int g = sp.g[sn];
+  const int64_t st = im.sn_start[sn];
+  const int wd = im.sn_w[sn];
+  double* __restrict__ w = im.work;
+  const double* __restrict__ M = (FWD ? im.DT : im.D) + im.sn_doff[sn];
+  // the dense block (forward reads column j as row j of DT, backward row j of D)
+  if (g == 1)
+    for (int e = threadIdx.x; e < wd * wd; e += kLevelThreads) S[e] = M[e];
+  // (1) this CTA's share of the off-block sums
   const int64_t* __restrict__ I = FWD ? im.Li : im.Ui;
   const double* __restrict__ X = FWD ? im.Lx : im.Ux;
-  double* const S = scratch + warp * kSnMax * kSnMax;
-  for (int gi = 0; gi < g1 - g0; ++gi) {
-    const int g = FWD ? g0 + gi : g1 - 1 - gi;
-    const int4* __restrict__ desc = FWD ? im.hg_fdesc : im.hg_bdesc;
-    const int q0 = FWD ? im.hg_frow_ptr[g] : im.hg_brow_ptr[g];
-    const int q1 = FWD ? im.hg_frow_ptr[g + 1] : im.hg_brow_ptr[g + 1];
-    // lpr lanes per row, 32 / lpr rows per warp at a time (the host picks lpr by the
-    // group's longest row); a row's entries are strided over its lanes, four loads in flight
-    const int lpr = FWD ? im.hg_flpr[g] : im.hg_blpr[g];
-    const int rpw = 32 / lpr, sub = lane & (lpr - 1), slot = lane / lpr;
-    for (int qb = q0 + warp * rpw; qb < q1; qb += nwarps * rpw) {
-      const int q = qb + slot;
-      double acc = 0.0;
-      int r = -1;
-      if (q < q1) {
-        const int4 dq = desc[q];
-        r = dq.x;
+  const int2* __restrict__ desc = FWD ? im.row_fdesc : im.row_bdesc;
+  const int lpr = sp.lpr[sn];
+  const int slots = kLevelThreads / lpr, slot = threadIdx.x / lpr, sub = threadIdx.x & (lpr - 1);
+  double* __restrict__ part = im.part + (g > 1 ? sp.pbase[sn] + (int64_t)c * kSnMax : 0);
+  for (int i0 = 0; i0 < wd; i0 += slots) {
+    const int i = i0 + slot;
+    double acc = 0.0;
+    if (i < wd) {
+      const int2 d = desc[st + i];
+      const int len = d.y - d.x;
+      const int pb = d.x + (int)((int64_t)len * c / g), pe = d.x + (int)((int64_t)len * (c + 1) / g);
 #pragma unroll 4
-        for (int p = dq.y + sub; p < dq.z; p += lpr) acc = fma(X[p], w[I[p]], acc);
-      }
-      for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lpr);
-      if (sub == 0 && r >= 0) w[r] -= acc;
+      for (int p = pb + sub; p < pe; p += lpr) acc = fma(X[p], w[I[p]], acc);
     }
-    __syncthreads();
-    for (int q = im.hg_sn_ptr[g] + warp; q < im.hg_sn_ptr[g + 1]; q += nwarps) {
-      const int sn = im.hg_sn[q];
-      double* __restrict__ ws = w + im.sn_start[sn];
-      const int wd = im.sn_w[sn];
-      // forward: column j of the block is row j of DT; backward: row j of L_ss is row j of D
-      const double* __restrict__ M = (FWD ? im.DT : im.D) + im.sn_doff[sn];
-      for (int e = lane; e < wd * wd; e += 32) S[e] = M[e];
-      __syncwarp();
-      for (int jj = 0; jj < wd; ++jj) {
-        const int j = FWD ? jj : wd - 1 - jj;
-        const double* Sj = S + j * wd;
-        const double xj = ws[j] * Sj[j];   // Sj[j] = 1 / L_jj
-        __syncwarp();
-        if (lane == 0) ws[j] = xj;
-        const int i = lane;
-        if (FWD ? (i > j && i < wd) : (i < j)) ws[i] = fma(-Sj[i], xj, ws[i]);
-        __syncwarp();
-      }
-      __syncwarp();   // the scratch is reused by the warp's next supernode
+    for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lpr);
+    if (sub == 0 && i < wd) {
+      if (g == 1)
+        T[i] = w[st + i] - acc;
+      else
+        part[i] = acc;
     }
-    __syncthreads();
   }
+  if (g > 1) {
+    // (2) the last CTA of the supernode takes over
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&im.cnt[sn], 1u) == (unsigned)(g - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int e = threadIdx.x; e < wd * wd; e += kLevelThreads) S[e] = M[e];
+    const double* __restrict__ p0 = im.part + sp.pbase[sn];
+    if (threadIdx.x < wd) {
+      double acc = 0.0;
+      for (int k = 0; k < g; ++k) acc += __ldcg(p0 + (int64_t)k * kSnMax + threadIdx.x);
+      T[threadIdx.x] = w[st + threadIdx.x] - acc;
+    }
+    if (threadIdx.x == 0) im.cnt[sn] = 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  // (3) substitution with the block (Sj[j] holds 1 / L_jj)
+  const int lane = threadIdx.x;
+  for (int jj = 0; jj < wd; ++jj) {
+    const int j = FWD ? jj : wd - 1 - jj;
+    const double* Sj = S + j * wd;
+    const double xj = T[j] * Sj[j];
+    __syncwarp();
+    if (lane == 0) T[j] = xj;
+    if (FWD ? (lane > j && lane < wd) : (lane < j)) T[lane] = fma(-Sj[lane], xj, T[lane]);
+    __syncwarp();
+  }
+  if (lane < wd) w[st + lane] = T[lane];
 }
 
-// A component's rows only couple to rows of the same component, so its vector can live in
-// shared memory, indexed by the permuted row (w = smem - r0).
-// The first kImexWarps * 32 * 32 doubles of the dynamic shared memory are the warps'
-// supernode scratch areas, the component's vector (when it fits) follows.
-extern __shared__ double imex_smem[];
-constexpr int kImexThreads = 512;
-constexpr int kImexScratch = kImexThreads / 32 * kSnMax * kSnMax;
-
-__global__ void __launch_bounds__(kImexThreads, 1) imex_solve_kernel(DevProblem pb, ImexDev im, double* __restrict__ out,
-                                                                  int in_smem) {
-  const int b = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int r0 = im.comp_ptr[b], r1 = im.comp_ptr[b + 1];
+// r = F^c_{k+1} - K^c Psi_pred on the permuted rows (a fixed summation order per row)
+__global__ void __launch_bounds__(256) imex_residual_kernel(DevProblem pb, ImexDev im) {
   const unsigned long long k = *((volatile unsigned long long*)pb.step);
   double fk1 = 0.0;
   if (pb.f_e > 0.0 && im.Fc) fk1 = ricker_imex((double)(k + 1) * pb.dt, pb.f_e);
-  double* w = in_smem ? imex_smem + kImexScratch - r0 : im.work;
-  // residual r = F_{k+1}^c - K^c Psi_pred (fixed summation order)
-  for (int r = r0 + tid; r < r1; r += blockDim.x) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
     double acc = im.Fc ? im.Fc[r] * fk1 : 0.0;
     for (int64_t e = im.g_ptr[r]; e < im.g_ptr[r + 1]; ++e) acc -= im.Y[im.g_idx[e]];
-    w[r] = acc;
+    im.work[r] = acc;
   }
-  __syncthreads();
-  // L y = r, then L^T x = y, by supernode height groups
-  block_solve<true>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
-  block_solve<false>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
-  // Newmark correction on the c-DOFs
+}
+
+// Newmark correction on the c-DOFs: Psi''^c = S^{-1} r (in work), Psi'^c += gamma dt Psi''^c,
+// Psi^c = Psi_pred^c + beta dt^2 Psi''^c; one thread advances the step counter
+__global__ void __launch_bounds__(256) imex_correct_kernel(DevProblem pb, ImexDev im, double* __restrict__ out) {
   bool bad = false;
-  for (int r = r0 + tid; r < r1; r += blockDim.x) {
-    int64_t ci = im.perm[r];
-    double a = w[r];
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ci = im.perm[r];
+    const double a = im.work[r];
     im.ac[ci] = a;
     im.vc[ci] = fma(im.gamma_dt, a, im.vc[ci]);
-    int64_t dof = im.c_dof[ci];
-    double nv = fma(im.beta_dt2, a, out[dof]);
+    const int64_t dof = im.c_dof[ci];
+    const double nv = fma(im.beta_dt2, a, out[dof]);
     out[dof] = nv;
     if (!isfinite(nv)) bad = true;
   }
   if (bad) atomicOr(pb.flags, 1);
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    unsigned prev = atomicAdd(pb.done, 1u);
-    if (prev == gridDim.x - 1) {
-      *pb.step = k + 1;
-      *pb.done = 0u;
-      __threadfence();
-    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *pb.step += 1ull;
+}
+
+// gather b[r] = in[c_dof[perm[r]]] * scal into work, or scatter out[c_dof[perm[r]]] = work[r]
+__global__ void __launch_bounds__(256) imex_gather_kernel(ImexDev im, const double* __restrict__ in,
+                                                          const double* __restrict__ scal) {
+  const double sc = scal ? *scal : 1.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x)
+    im.work[r] = in[im.c_dof[im.perm[r]]] * sc;
+}
+
+__global__ void __launch_bounds__(256) imex_scatter_kernel(ImexDev im, double* __restrict__ out) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x)
+    out[im.c_dof[im.perm[r]]] = im.work[r];
+}
+
+static int rows_grid(const ImexDev& im) { return (int)std::min<int64_t>((im.n_rows + 255) / 256, 4096); }
+
+// the launches of one triangular solve, height by height (the CTA ranges live on the host)
+static cudaError_t launch_levels(const ImexDev& im, bool fwd, cudaStream_t st) {
+  const int32_t* ptr = fwd ? im.fs.cta_ptr_host : im.bs.cta_ptr_host;
+  for (int hh = 0; hh < im.n_heights; ++hh) {
+    const int h = fwd ? hh : im.n_heights - 1 - hh;
+    const int c0 = ptr[h], n = ptr[h + 1] - ptr[h];
+    if (n <= 0) continue;
+    if (fwd)
+      imex_level_kernel<true><<<n, kLevelThreads, 0, st>>>(im, c0);
+    else
+      imex_level_kernel<false><<<n, kLevelThreads, 0, st>>>(im, c0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 // One triangular solve with the Cholesky factor L of S (permuted order), for the power
-// iteration of the consistent-mass CDM (S = M^cc there): one CTA per component; the right-
-// hand side is b[r] = in[c_dof[perm[r]]] * scal, the solution of L w = b (forward) or of
-// L^T w = b (backward) is written to out[c_dof[perm[r]]].
-__global__ void __launch_bounds__(kImexThreads) imex_tri_kernel(ImexDev im, const double* __restrict__ in,
-                                                        const double* __restrict__ scal,
-                                                        double* __restrict__ out, int backward, int in_smem) {
-  const int b = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int r0 = im.comp_ptr[b], r1 = im.comp_ptr[b + 1];
-  const double sc = scal ? *scal : 1.0;
-  double* w = in_smem ? imex_smem + kImexScratch - r0 : im.work;
-  for (int r = r0 + tid; r < r1; r += blockDim.x) w[r] = in[im.c_dof[im.perm[r]]] * sc;
-  __syncthreads();
-  if (!backward)
-    block_solve<true>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
-  else
-    block_solve<false>(im, im.comp_hg[b], im.comp_hg[b + 1], w, imex_smem, lane, warp, nwarps);
-  for (int r = r0 + tid; r < r1; r += blockDim.x) out[im.c_dof[im.perm[r]]] = w[r];
-}
-
-// dynamic shared memory: the warps' scratch, then the largest component's vector if it fits
-// (else the vector stays in the global work array)
-static size_t imex_vec_bytes(const ImexDev& im) {
-  const size_t bytes = (size_t)im.max_comp * sizeof(double);
-  return bytes + kImexScratch * sizeof(double) <= (size_t)220 * 1024 ? bytes : 0;
-}
-
-template <typename KernelT>
-static cudaError_t imex_smem_config(KernelT kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-}
-
+// iteration of the consistent-mass CDM (S = M^cc there): the right-hand side is
+// b[r] = in[c_dof[perm[r]]] * scal, the solution of L w = b (forward) or of L^T w = b
+// (backward) is written to out[c_dof[perm[r]]].
 cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* scal, double* out, bool backward,
                             cudaStream_t st) {
-  if (im.n_comp == 0) return cudaSuccess;
-  static const cudaError_t cfg = imex_smem_config(imex_tri_kernel);
-  if (cfg != cudaSuccess) return cfg;
-  const size_t vb = imex_vec_bytes(im);
-  imex_tri_kernel<<<im.n_comp, kImexThreads, kImexScratch * sizeof(double) + vb, st>>>(im, in, scal, out,
-                                                                                     backward ? 1 : 0, vb > 0 ? 1 : 0);
+  if (im.n_rows == 0) return cudaSuccess;
+  imex_gather_kernel<<<rows_grid(im), 256, 0, st>>>(im, in, scal);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_levels(im, !backward, st);
+  if (e != cudaSuccess) return e;
+  imex_scatter_kernel<<<rows_grid(im), 256, 0, st>>>(im, out);
   return cudaGetLastError();
 }
 
@@ -230,11 +242,13 @@ cudaError_t launch_imex_cell_apply(const DevProblem& pb, const ImexDev& im, cons
 }
 
 cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* out, cudaStream_t st) {
-  if (im.n_comp == 0) return cudaSuccess;
-  static const cudaError_t cfg = imex_smem_config(imex_solve_kernel);
-  if (cfg != cudaSuccess) return cfg;
-  const size_t vb = imex_vec_bytes(im);
-  imex_solve_kernel<<<im.n_comp, kImexThreads, kImexScratch * sizeof(double) + vb, st>>>(pb, im, out, vb > 0 ? 1 : 0);
+  if (im.n_rows == 0) return cudaSuccess;
+  imex_residual_kernel<<<rows_grid(im), 256, 0, st>>>(pb, im);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_levels(im, true, st);
+  if (e == cudaSuccess) e = launch_levels(im, false, st);
+  if (e != cudaSuccess) return e;
+  imex_correct_kernel<<<rows_grid(im), 256, 0, st>>>(pb, im, out);
   return cudaGetLastError();
 }
 

@@ -154,10 +154,7 @@ void Handle::build_device() {
     D.n_cells = (int)I.ccells.size();
     D.cells = upload(I.ccells);
     D.Y = static_cast<double*>(dalloc(std::max<size_t>(I.ccells.size(), 1) * s.n_loc * sizeof(double)));
-    D.n_comp = (int)I.comp_ptr.size() - 1;
-    D.comp_ptr = upload(I.comp_ptr);
-    D.max_comp = 0;
-    for (int c = 0; c < D.n_comp; ++c) D.max_comp = std::max(D.max_comp, I.comp_ptr[c + 1] - I.comp_ptr[c]);
+    D.n_rows = I.n_c;
     D.g_ptr = upload(I.g_ptr);
     D.g_idx = upload(I.g_idx);
     D.work = static_cast<double*>(dalloc(I.n_c * sizeof(double)));
@@ -439,7 +436,7 @@ size_t Handle::planned_device_bytes() const {
   if (imex) {
     const ImexData& I = imex_host;
     const int64_t ncell = (int64_t)I.ccells.size();
-    b += arr(ncell, 8) + arr(ncell, 8) * nl + arr((int64_t)I.comp_ptr.size(), 4) + arr((int64_t)I.g_ptr.size(), 8) +
+    b += arr(ncell, 8) + arr(ncell, 8) * nl + arr((int64_t)I.g_ptr.size(), 8) +
          arr((int64_t)I.g_idx.size(), 4) + 3 * arr(I.n_c, 8) + arr((int64_t)I.perm.size(), 8) +
          arr((int64_t)I.c_dof.size(), 8);
   }
@@ -476,6 +473,9 @@ void Handle::imex_upload_factor() {
   const ImexData& I = imex_host;
   const SparseChol& L = I.chol;
   ImexDev& D = imex_dev;
+  D.n_heights = (int)I.gh_sn_ptr.size() - 1;
+  D.fs.cta_ptr_host = I.fsplit.cta_ptr.data();
+  D.bs.cta_ptr_host = I.bsplit.cta_ptr.data();
   size_t nnz = L.Lx.size();
   if (imex_nnz_alloc != nnz) {
     // the pattern, the order and the supernodes do not depend on dt: allocated once
@@ -488,35 +488,32 @@ void Handle::imex_upload_factor() {
     D.Ux = static_cast<double*>(dalloc(nnz * sizeof(double)));
     D.D = static_cast<double*>(dalloc(std::max<size_t>(nd, 1) * sizeof(double)));
     D.DT = static_cast<double*>(dalloc(std::max<size_t>(nd, 1) * sizeof(double)));
-    D.f_off_end = static_cast<int64_t*>(dalloc(I.n_c * sizeof(int64_t)));
-    D.b_off_beg = static_cast<int64_t*>(dalloc(I.n_c * sizeof(int64_t)));
     D.sn_start = upload(I.sn_start);
     D.sn_w = upload(I.sn_size);
     D.sn_doff = upload(I.sn_doff);
-    D.comp_hg = upload(I.comp_hg);
-    D.hg_sn_ptr = upload(I.hg_sn_ptr);
-    D.hg_sn = upload(I.hg_sn);
-    D.hg_frow_ptr = upload(I.hg_frow_ptr);
-    D.hg_frows = upload(I.hg_frows);
-    D.hg_brow_ptr = upload(I.hg_brow_ptr);
-    D.hg_brows = upload(I.hg_brows);
-    D.hg_flpr = upload(I.hg_flpr);
-    D.hg_blpr = upload(I.hg_blpr);
-    // one 16-byte descriptor per listed row (its entry range), so that a row costs one load
-    // before its entries (the pattern does not depend on dt)
+    for (int dir = 0; dir < 2; ++dir) {
+      const ImexSplit& sp = dir == 0 ? I.fsplit : I.bsplit;
+      ImexSplitDev& sd = dir == 0 ? D.fs : D.bs;
+      sd.cta = reinterpret_cast<const int2*>(upload(sp.cta));
+      sd.g = upload(sp.g);
+      sd.lpr = upload(sp.lpr);
+      sd.pbase = upload(sp.pbase);
+    }
+    D.part = static_cast<double*>(dalloc(std::max<int64_t>({I.fsplit.n_parts, I.bsplit.n_parts, 1}) * sizeof(double)));
+    D.cnt = static_cast<unsigned int*>(dalloc(std::max<size_t>(I.sn_start.size(), 1) * sizeof(unsigned int)));
+    check(cudaMemsetAsync(D.cnt, 0, std::max<size_t>(I.sn_start.size(), 1) * sizeof(unsigned int), stream), "memset");
+    // one 8-byte descriptor per row (its off-block entry range), so that a row costs one
+    // load before its entries (the pattern does not depend on dt)
     if (nnz > (size_t)INT32_MAX) throw std::runtime_error("IMEX factor too large for 32-bit entry offsets");
-    auto desc = [&](const std::vector<int32_t>& rows, bool fwd) {
-      std::vector<int32_t> v(4 * std::max<size_t>(rows.size(), 1), 0);
-      for (size_t q = 0; q < rows.size(); ++q) {
-        const int32_t r = rows[q];
-        v[4 * q] = r;
-        v[4 * q + 1] = (int32_t)(fwd ? L.Lp[r] : I.b_off_beg[r]);
-        v[4 * q + 2] = (int32_t)(fwd ? I.f_off_end[r] : L.Up[r + 1]);
-      }
-      return v;
-    };
-    D.hg_fdesc = reinterpret_cast<const int4*>(upload(desc(I.hg_frows, true)));
-    D.hg_bdesc = reinterpret_cast<const int4*>(upload(desc(I.hg_brows, false)));
+    std::vector<int32_t> fd(2 * std::max<int64_t>(I.n_c, 1), 0), bd(fd.size(), 0);
+    for (int64_t r = 0; r < I.n_c; ++r) {
+      fd[2 * r] = (int32_t)L.Lp[r];
+      fd[2 * r + 1] = (int32_t)I.f_off_end[r];
+      bd[2 * r] = (int32_t)I.b_off_beg[r];
+      bd[2 * r + 1] = (int32_t)L.Up[r + 1];
+    }
+    D.row_fdesc = reinterpret_cast<const int2*>(upload(fd));
+    D.row_bdesc = reinterpret_cast<const int2*>(upload(bd));
     imex_nnz_alloc = nnz;
   }
   auto cp = [&](const void* dst, const void* src, size_t bytes) {
@@ -529,9 +526,8 @@ void Handle::imex_upload_factor() {
   cp(D.Ui, L.Ui.data(), nnz * sizeof(int64_t));
   cp(D.Ux, L.Ux.data(), nnz * sizeof(double));
   cp(D.D, I.sn_D.data(), I.sn_D.size() * sizeof(double));
+  check(cudaMemsetAsync(D.cnt, 0, std::max<size_t>(I.sn_start.size(), 1) * sizeof(unsigned int), stream), "memset");
   cp(D.DT, I.sn_DT.data(), I.sn_DT.size() * sizeof(double));
-  cp(D.f_off_end, I.f_off_end.data(), I.f_off_end.size() * sizeof(int64_t));
-  cp(D.b_off_beg, I.b_off_beg.data(), I.b_off_beg.size() * sizeof(int64_t));
   check(cudaStreamSynchronize(stream), "factor upload");
 }
 
@@ -911,10 +907,8 @@ int ibfem_info(const ibfem_t* h, ibfem_info_t* out) {
   if (h->imex) {
     out->n_c = h->imex_host.n_c;
     out->nnz_L = (int64_t)h->imex_host.chol.Lx.size();
-    int32_t steps = 0;   // height groups of the largest component: sequential steps of a solve
-    const ImexData& I = h->imex_host;
-    for (size_t c = 0; c + 1 < I.comp_hg.size(); ++c) steps = std::max(steps, I.comp_hg[c + 1] - I.comp_hg[c]);
-    out->n_levels = steps;
+    // heights of the dissection tree: the launches of one triangular solve
+    out->n_levels = (int32_t)h->imex_host.gh_sn_ptr.size() - 1;
   }
   out->shared_device_bytes = h->shared ? h->shared->bytes : 0;
   out->device_bytes = h->opt.host_only ? h->planned_device_bytes() : h->device_bytes + out->shared_device_bytes;
