@@ -1307,46 +1307,92 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
       if (d.sn_height[q] == h) d.gh_sn.push_back((int32_t)q);
     d.gh_sn_ptr.push_back((int32_t)d.gh_sn.size());
   }
-  // work split of the off-block sums, per direction: a supernode whose rows hold E entries
-  // gets g = ceil(E / kImexCtaEntries) CTAs (at most kImexMaxSplit), each taking the same
-  // fraction of every row; lanes per row 4, 8 or 32 by the longest share of a row (short
-  // rows share a warp, their loads in flight together); partial sums of split supernodes at
-  // sn_pbase (32 per CTA); the CTAs of each height listed in height order
+  // work split of the off-block sums, per direction: the tpr threads of a row take its
+  // entries in turn, and a supernode gets g CTAs, each with the same fraction of every row,
+  // g chosen so that no thread sums more than kImexThreadEntries entries (its loads are
+  // issued together, before the CTA waits); partial sums of split supernodes at pbase (32
+  // per CTA).
+  //
+  // Waits: with the elimination tree of L (parent(j) = the first row below the diagonal in
+  // column j), an entry L_ij != 0 (i > j) makes i an ancestor of j, and the path from j up
+  // to i climbs in row order.  So in the forward sweep a supernode needs only the supernodes
+  // of the rows whose parent lies in it (every other row it reads is below one of those on
+  // a tree path, finished before them), and in the backward sweep only the supernodes of
+  // its rows' parents.  CTAs take supernodes by height of the dissection tree (forward
+  // upwards, backward downwards; the chains of every component start at once) if that order
+  // is topological for the waits, else by index (always topological: a wait is on a lower
+  // index forward, a higher one backward): every wait is on a supernode taken earlier.
+  std::vector<int32_t> sn_of(d.n_c, 0);
+  for (size_t q = 0; q < nsn; ++q)
+    for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) sn_of[r] = (int32_t)q;
+  std::vector<std::vector<int32_t>> fdep(nsn), bdep(nsn);
+  for (int64_t j = 0; j < d.n_c; ++j) {
+    if (L.Up[j + 1] - L.Up[j] < 2) continue;          // a root: no entry below the diagonal
+    const int64_t par = L.Ui[L.Up[j] + 1];
+    const int32_t a = sn_of[j], b = sn_of[par];
+    if (a == b) continue;
+    fdep[b].push_back(a);
+    bdep[a].push_back(b);
+  }
   for (int dir = 0; dir < 2; ++dir) {
     ImexSplit& sp = dir == 0 ? d.fsplit : d.bsplit;
     sp.g.assign(nsn, 1);
-    sp.lpr.assign(nsn, 4);
+    sp.tpr.assign(nsn, 32);
     sp.pbase.assign(nsn, 0);
     int64_t parts = 0;
     for (size_t q = 0; q < nsn; ++q) {
-      int64_t tot = 0, lng = 0;
-      for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) {
-        const int64_t len = dir == 0 ? d.f_off_end[r] - L.Lp[r] : L.Up[r + 1] - d.b_off_beg[r];
-        tot += len;
-        lng = std::max(lng, len);
-      }
-      const int64_t g = std::min<int64_t>(kImexMaxSplit, std::max<int64_t>(1, (tot + kImexCtaEntries - 1) / kImexCtaEntries));
-      const int64_t share = (lng + g - 1) / g;
+      int64_t lng = 0;
+      for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r)
+        lng = std::max(lng, dir == 0 ? d.f_off_end[r] - L.Lp[r] : L.Up[r + 1] - d.b_off_beg[r]);
+      int tpr = 32;
+      while (tpr > 8 && tpr * d.sn_size[q] > 256) tpr >>= 1;
+      const int64_t per_cta = kImexThreadEntries * tpr;
+      const int64_t g = std::min<int64_t>(kImexMaxSplit, std::max<int64_t>(1, (lng + per_cta - 1) / per_cta));
       sp.g[q] = (int32_t)g;
-      sp.lpr[q] = share <= 48 ? 4 : (share <= 192 ? 8 : 32);
+      sp.tpr[q] = tpr;
       if (g > 1) {
         sp.pbase[q] = parts;
         parts += g * 32;
       }
     }
     sp.n_parts = parts;
-    sp.cta.clear();
-    sp.cta_ptr.assign(1, 0);
-    for (int h = 0; h <= hmax; ++h) {
-      for (int32_t k = d.gh_sn_ptr[h]; k < d.gh_sn_ptr[h + 1]; ++k) {
-        const int32_t q = d.gh_sn[k];
-        for (int32_t c = 0; c < sp.g[q]; ++c) {
-          sp.cta.push_back(q);
-          sp.cta.push_back(c);
-        }
-      }
-      sp.cta_ptr.push_back((int32_t)(sp.cta.size() / 2));
+    auto& deps = dir == 0 ? fdep : bdep;
+    sp.dep_ptr.assign(1, 0);
+    sp.dep.clear();
+    for (size_t q = 0; q < nsn; ++q) {
+      std::vector<int32_t>& v = deps[q];
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      sp.dep.insert(sp.dep.end(), v.begin(), v.end());
+      sp.dep_ptr.push_back((int32_t)sp.dep.size());
     }
+    // order: by height (forward ascending, backward descending), ties by index
+    sp.order.resize(nsn);
+    for (size_t q = 0; q < nsn; ++q) sp.order[q] = (int32_t)q;
+    std::stable_sort(sp.order.begin(), sp.order.end(), [&](int32_t a, int32_t b) {
+      return dir == 0 ? d.sn_height[a] < d.sn_height[b] : d.sn_height[a] > d.sn_height[b];
+    });
+    if (dir == 1) {
+      // descending index within a height
+      size_t k0 = 0;
+      while (k0 < nsn) {
+        size_t k1 = k0;
+        while (k1 < nsn && d.sn_height[sp.order[k1]] == d.sn_height[sp.order[k0]]) ++k1;
+        std::reverse(sp.order.begin() + k0, sp.order.begin() + k1);
+        k0 = k1;
+      }
+    }
+    std::vector<int32_t> pos(nsn, 0);
+    for (size_t k = 0; k < nsn; ++k) pos[sp.order[k]] = (int32_t)k;
+    bool topo = true;
+    for (size_t q = 0; q < nsn && topo; ++q)
+      for (int32_t k = sp.dep_ptr[q]; k < sp.dep_ptr[q + 1]; ++k)
+        if (pos[sp.dep[k]] >= pos[q]) {
+          topo = false;
+          break;
+        }
+    if (!topo)
+      for (size_t q = 0; q < nsn; ++q) sp.order[q] = (int32_t)(dir == 0 ? q : nsn - 1 - q);
   }
   return true;
 }

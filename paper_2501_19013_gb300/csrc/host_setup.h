@@ -116,19 +116,23 @@ bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vecto
 // the consistent M^cc and K^cc on it, and the Cholesky factor of S = M^cc + beta dt^2 K^cc
 // in a fill-reducing order (connected components, then geometric nested dissection), with
 // the supernodes of that order for the block triangular solves.
-// Entries of off-block sums per CTA of the GPU block solve, and the most CTAs one
-// supernode's sums are split over.
-constexpr int64_t kImexCtaEntries = 2048;
+// Off-block entries of one row that one thread of the GPU block solve sums (the host picks
+// the CTAs per supernode so that no thread has more), and the most CTAs one supernode's
+// sums are split over (beyond that the threads loop).
+constexpr int64_t kImexThreadEntries = 8;
 constexpr int64_t kImexMaxSplit = 256;
 
-// Split of one direction's off-block sums (forward: L y = b; backward: L^T x = y).
+// One direction's sweep of the block solve (forward: L y = b; backward: L^T x = y): the
+// split of each supernode's off-block sums over CTAs, the supernodes each one waits for, and
+// the order in which CTAs take the supernodes (a topological order of those waits).
 struct ImexSplit {
   std::vector<int32_t> g;        // per supernode: CTAs
-  std::vector<int32_t> lpr;      // per supernode: lanes per row (4, 8 or 32)
+  std::vector<int32_t> tpr;      // per supernode: threads per row (256 / wd rounded down to
+                                 // a power of two, at most 32)
   std::vector<int64_t> pbase;    // per supernode split over g > 1 CTAs: first partial sum
   int64_t n_parts = 0;           // partial sums of all split supernodes
-  std::vector<int32_t> cta;      // per CTA of the level launches: {supernode, share}
-  std::vector<int32_t> cta_ptr;  // per height: first CTA (heights + 1 entries)
+  std::vector<int32_t> dep_ptr, dep;   // per supernode: the supernodes it waits for
+  std::vector<int32_t> order;    // supernodes in the order their CTAs are taken
 };
 
 struct ImexData {

@@ -78,13 +78,33 @@ struct BatchCtl {
 };
 
 // Device view of the IMEX partition and factor (kernels_imex.cu).
-// One direction's CTAs of the block solve (host-side ImexSplit on the device).
+// One CTA of a sweep of the block solve: its supernode sn (first row st, wd rows, dense
+// block at doff), the threads per row of its off-block sums, its share c of the g CTAs of the
+// supernode, for g > 1 the supernode's first partial sum (32 per CTA; pbase / 32 is the
+// supernode's arrival counter), and the supernodes it waits for (dep[dep_beg, dep_beg +
+// dep_n) of its direction).
+struct __align__(16) LevelTask {
+  int32_t st;
+  int32_t wd_tpr;            // wd | tpr << 16
+  int32_t c, g;
+  int64_t doff, pbase;
+  int32_t sn, dep_beg, dep_n, pad;
+};
+
+// One direction's sweep (CTAs in the order they take tickets).
 struct ImexSplitDev {
-  const int2* cta;           // per CTA: {supernode, share c of g}
-  const int32_t* g;          // per supernode: CTAs its off-block sums are split over
-  const int32_t* lpr;        // per supernode: lanes per row
-  const int64_t* pbase;      // per split supernode: first partial sum (32 per CTA)
-  const int32_t* cta_ptr_host;   // host array: heights + 1 offsets into cta
+  const LevelTask* task;
+  const int32_t* dep;
+  unsigned int* done;        // per supernode: the epoch of the sweep that finished it
+  int n_tasks;
+};
+
+// Sweep control in device memory: the ticket counters of the two sweeps and the epoch of
+// the current solve (the kernel before a solve resets the tickets and advances the epoch).
+struct SweepCtl {
+  unsigned int tick[2];
+  unsigned int epoch;
+  unsigned int pad;
 };
 
 struct ImexDev {
@@ -96,27 +116,24 @@ struct ImexDev {
   const int32_t* g_idx;
   const double* Fc;          // spatial load on the c-DOFs (permuted rows), or null
   double* work;              // n_c
-  const int64_t *Lp, *Li;    // L by rows, diagonal last
+  const int32_t* Li;         // L by rows, diagonal last (column indices)
   const double* Lx;
-  const int64_t *Up, *Ui;    // L^T by rows, diagonal first
+  const int32_t* Ui;         // L^T by rows, diagonal first
   const double* Ux;
   // block triangular solves: supernodes (contiguous permuted rows of at most 32) with the
-  // dense diagonal block of L (row-major w x w at sn_doff, 1 / L_jj on the diagonal) and
-  // its transpose DT; per row the range of its off-block entries in L (forward) and in L^T
-  // (backward); per direction the CTAs of each height of the dissection tree (one launch
-  // per height, the ranges on the host), the split of each supernode's off-block sums over
-  // its CTAs, their partial sums and one arrival counter per supernode
-  const int64_t* sn_start;
-  const int32_t* sn_w;
-  const int64_t* sn_doff;
+  // dense diagonal block of L (row-major w x w at the task's doff, 1 / L_jj on the
+  // diagonal) and its transpose DT; per row the range of its off-block entries in L
+  // (forward) and in L^T (backward); per direction the CTAs of its sweep, the partial sums
+  // of split supernodes and one arrival counter per split supernode
   const double* D;
   const double* DT;
   const int2* row_fdesc;     // {Lp[r], end of the off-block entries of row r}
   const int2* row_bdesc;     // {start of the off-block entries of row r of L^T, Up[r + 1]}
   ImexSplitDev fs, bs;       // forward, backward
   double* part;
-  unsigned int* cnt;         // zero between launches (the last CTA of a supernode resets it)
-  int n_heights;
+  unsigned int* cnt;         // per split supernode; zero between launches (its last CTA resets it)
+  SweepCtl* ctl;
+  int* flags;                // bit 1: a bounded wait gave up
   const int64_t* perm;       // permuted row -> c index
   const int64_t* c_dof;      // c index -> lattice DOF
   double* vc;

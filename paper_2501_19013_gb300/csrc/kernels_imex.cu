@@ -7,8 +7,8 @@
 //                       FP64), x = [Psi_{k+1}^d ; Psi_pred^c];
 //   * imex_solve      : the residual r = F^c_{k+1} - K^c Psi_pred gathered in a fixed
 //                       order, the forward and backward solves with the host Cholesky
-//                       factor of S = M^cc + beta dt^2 K^cc by supernode blocks (one launch
-//                       per height of the dissection tree), and the Newmark correction
+//                       factor of S = M^cc + beta dt^2 K^cc by supernode blocks (one
+//                       dependency-driven launch per sweep), and the Newmark correction
 //                       Psi''^c = S^{-1} r, Psi'^c = Psi'_pred^c + gamma dt Psi''^c,
 //                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c, which advances the step
 //                       counter.
@@ -54,102 +54,165 @@ __global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, Ime
 }
 
 // Block triangular solves over the supernodes of the nested-dissection order (each leaf
-// block and each separator, a contiguous run of at most 32 rows, depends only on the
-// supernodes below it in the dissection tree).  One launch per tree height, over every
-// component: the launches of lower (forward) or higher (backward) heights have completed,
-// so every row a supernode reads is final.  For each supernode:
-//   (1) its rows' entries outside the diagonal block (forward: columns before it; backward,
-//       rows of L^T: columns after it) are summed by g CTAs, each taking the same fraction
-//       of every row, with 4, 8 or 32 lanes on a row (g and the lanes fixed on the host by
-//       the entry counts: the separators near the top of the tree reach far back and get
-//       many CTAs);
-//   (2) with g > 1 each CTA stores its 32 partial sums and counts itself in; the last CTA
-//       to arrive adds the partials in share order (the sum does not depend on the arrival
-//       order) and resets the counter;
+// block and each separator, a contiguous run of at most 32 rows).  One launch per sweep:
+// every CTA takes a ticket and with it the next task of a topological order of the
+// supernodes (by height of the dissection tree where that order is topological); it loads
+// what does not depend on other supernodes (its dense diagonal block, its rows' right-hand
+// sides and its share of the factor's entries), then waits, with bounded polls, for the
+// done flags of the supernodes its rows depend on (edges of the elimination tree between
+// supernodes, all taken by lower tickets: CTAs already running, so every wait ends), and:
+//   (1) sums its share of its rows' entries outside the diagonal block (forward: columns
+//       before it; backward, rows of L^T: columns after it): the g CTAs of a supernode each
+//       take the same fraction of every row, tpr threads per row with at most
+//       kImexThreadEntries entries each (g fixed on the host), so that one round of
+//       gathers of the solution follows the wait;
+//   (2) with g > 1 stores its 32 partial sums and counts itself in; the last CTA to arrive
+//       adds the partials in a fixed order (it does not depend on the arrival order) and
+//       resets the counter;
 //   (3) that CTA solves t_i = w_i - sum_i with the dense diagonal block by substitution in
-//       shared memory (walking its columns forward, its rows backward, lanes over the other
-//       rows) and writes the block's rows back.
-// FWD: L y = b; else L^T x = y.  No CTA waits on another.
-constexpr int kSnMax = 32;          // rows of a supernode (the host splits longer runs)
-constexpr int kLevelThreads = 256;  // threads of a level CTA
+//       registers, writes the block's rows back and releases the supernode's done flag
+//       with the epoch of this solve.
+// The solution vector is read through L2 only (ld.global.cg): rows become final while the
+// kernel runs, and an L1 line could still hold a neighbour's earlier value.
+// FWD: L y = b; else L^T x = y.
+constexpr int kSnMax = 32;           // rows of a supernode (the host splits longer runs)
+constexpr int kLevelThreads = 256;   // threads of a sweep CTA
+constexpr int kSweepK = 8;           // entries per thread and row share (kImexThreadEntries)
+constexpr int kSweepPolls = 1 << 21; // polls of one wait before it gives up (about 1 s)
+
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kLevelThreads) imex_level_kernel(ImexDev im, int c0) {
+__global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(ImexDev im) {
   __shared__ double S[kSnMax * kSnMax];
   __shared__ double T[kSnMax];
-  __shared__ int last;
+  __shared__ int ticket, last;
   const ImexSplitDev& sp = FWD ? im.fs : im.bs;
-  const int2 task = sp.cta[c0 + blockIdx.x];
-  const int sn = task.x, c = task.y;
-  const int g = sp.g[sn];
-  const int64_t st = im.sn_start[sn];
-  const int wd = im.sn_w[sn];
-  double* __restrict__ w = im.work;
-  const double* __restrict__ M = (FWD ? im.DT : im.D) + im.sn_doff[sn];
-  // the dense block (forward reads column j as row j of DT, backward row j of D)
-  if (g == 1)
-    for (int e = threadIdx.x; e < wd * wd; e += kLevelThreads) S[e] = M[e];
-  // (1) this CTA's share of the off-block sums
-  const int64_t* __restrict__ I = FWD ? im.Li : im.Ui;
-  const double* __restrict__ X = FWD ? im.Lx : im.Ux;
-  const int2* __restrict__ desc = FWD ? im.row_fdesc : im.row_bdesc;
-  const int lpr = sp.lpr[sn];
-  const int slots = kLevelThreads / lpr, slot = threadIdx.x / lpr, sub = threadIdx.x & (lpr - 1);
-  double* __restrict__ part = im.part + (g > 1 ? sp.pbase[sn] + (int64_t)c * kSnMax : 0);
-  for (int i0 = 0; i0 < wd; i0 += slots) {
-    const int i = i0 + slot;
-    double acc = 0.0;
-    if (i < wd) {
-      const int2 d = desc[st + i];
-      const int len = d.y - d.x;
-      const int pb = d.x + (int)((int64_t)len * c / g), pe = d.x + (int)((int64_t)len * (c + 1) / g);
-#pragma unroll 4
-      for (int p = pb + sub; p < pe; p += lpr) acc = fma(X[p], w[I[p]], acc);
-    }
-    for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lpr);
-    if (sub == 0 && i < wd) {
-      if (g == 1)
-        T[i] = w[st + i] - acc;
-      else
-        part[i] = acc;
-    }
+  if (threadIdx.x == 0) ticket = (int)atomicAdd(&im.ctl->tick[FWD ? 0 : 1], 1u);
+  __syncthreads();
+  if (ticket >= sp.n_tasks) {   // the tickets were not reset before this sweep
+    if (threadIdx.x == 0) atomicOr(im.flags, 2);
+    return;
   }
-  if (g > 1) {
-    // (2) the last CTA of the supernode takes over
-    __threadfence();
+  const LevelTask tk = sp.task[ticket];
+  const unsigned int ep = *((volatile unsigned int*)&im.ctl->epoch);
+  const int st = tk.st, wd = tk.wd_tpr & 0xffff, tpr = tk.wd_tpr >> 16, c = tk.c, g = tk.g;
+  double* __restrict__ w = im.work;
+  // independent of other supernodes: the dense block (forward reads column j as row j of
+  // DT, backward row j of D), the rows' right-hand sides (only this supernode writes them)
+  // and the first round of this thread's entries
+  const double* __restrict__ M = (FWD ? im.DT : im.D) + tk.doff;
+  for (int e = threadIdx.x; e < wd * wd; e += kLevelThreads) S[e] = M[e];
+  const double rhs = threadIdx.x < wd ? __ldcg(w + st + threadIdx.x) : 0.0;
+  const int32_t* __restrict__ I = FWD ? im.Li : im.Ui;
+  const double* __restrict__ X = FWD ? im.Lx : im.Ux;
+  const int row = threadIdx.x / tpr, sub = threadIdx.x & (tpr - 1);
+  int pb = 0, pe = 0;
+  if (row < wd) {
+    const int2 d = (FWD ? im.row_fdesc : im.row_bdesc)[st + row];
+    const int len = d.y - d.x;
+    pb = d.x + (int)((int64_t)len * c / g);
+    pe = d.x + (int)((int64_t)len * (c + 1) / g);
+  }
+  double xv[kSweepK];
+  int iv[kSweepK];
+#pragma unroll
+  for (int k = 0; k < kSweepK; ++k) {
+    const int p = pb + sub + k * tpr;
+    xv[k] = p < pe ? X[p] : 0.0;
+    iv[k] = p < pe ? I[p] : -1;
+  }
+  // the supernodes this one reads: relaxed polls, one acquire fence once they are done
+  bool waited = false;
+  for (int k = threadIdx.x; k < tk.dep_n; k += kLevelThreads) {
+    const unsigned int* f = sp.done + sp.dep[tk.dep_beg + k];
+    int it = 0;
+    while (ld_relaxed_u32(f) != ep) {
+      if (++it >= kSweepPolls) {
+        atomicOr(im.flags, 2);
+        break;
+      }
+      __nanosleep(32);
+    }
+    waited = true;
+  }
+  if (waited) fence_acq_rel_gpu();
+  __syncthreads();
+  // (1) this CTA's share of the off-block sums
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < kSweepK; ++k)
+    if (iv[k] >= 0) acc = fma(xv[k], __ldcg(w + iv[k]), acc);
+  for (int p = pb + sub + kSweepK * tpr; p < pe; p += tpr) acc = fma(X[p], __ldcg(w + I[p]), acc);
+  for (int o = tpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, tpr);
+  if (g == 1) {
+    if (sub == 0 && row < wd) T[row] = acc;
+  } else {
+    // (2) partial sums; the last CTA of the supernode takes over
+    if (sub == 0 && row < wd) {
+      im.part[tk.pbase + (int64_t)c * kSnMax + row] = acc;
+      fence_acq_rel_gpu();
+    }
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&im.cnt[sn], 1u) == (unsigned)(g - 1);
+    unsigned int* cnt = im.cnt + (tk.pbase >> 5);
+    if (threadIdx.x == 0) {
+      last = atomicAdd(cnt, 1u) == (unsigned)(g - 1);
+      if (last) fence_acq_rel_gpu();
+    }
     __syncthreads();
     if (!last) return;
-    __threadfence();
-    for (int e = threadIdx.x; e < wd * wd; e += kLevelThreads) S[e] = M[e];
-    const double* __restrict__ p0 = im.part + sp.pbase[sn];
-    if (threadIdx.x < wd) {
-      double acc = 0.0;
-      for (int k = 0; k < g; ++k) acc += __ldcg(p0 + (int64_t)k * kSnMax + threadIdx.x);
-      T[threadIdx.x] = w[st + threadIdx.x] - acc;
-    }
-    if (threadIdx.x == 0) im.cnt[sn] = 0u;
+    // 8 threads per row, each over every 8th share in order, then a fixed shuffle tree
+    const int r8 = threadIdx.x >> 3, q8 = threadIdx.x & 7;
+    double s8 = 0.0;
+    if (r8 < wd)
+      for (int k = q8; k < g; k += 8) s8 += __ldcg(im.part + tk.pbase + (int64_t)k * kSnMax + r8);
+    for (int o = 4; o > 0; o >>= 1) s8 += __shfl_down_sync(0xffffffffu, s8, o, 8);
+    if (q8 == 0 && r8 < wd) T[r8] = s8;
+    if (threadIdx.x == 0) *cnt = 0u;
   }
   __syncthreads();
   if (threadIdx.x >= 32) return;
-  // (3) substitution with the block (Sj[j] holds 1 / L_jj)
+  // (3) substitution with the block in registers: lane l holds row l; at step j lane j's
+  // value is final, x_j = t_j / L_jj goes to every lane by a shuffle and the lanes below
+  // (forward) or above (backward) subtract L_lj x_j (S[j wd + l]; S[l wd + l] = 1 / L_ll)
   const int lane = threadIdx.x;
+  double t = lane < wd ? rhs - T[lane] : 0.0;
+  const double dl = lane < wd ? S[lane * wd + lane] : 0.0;
   for (int jj = 0; jj < wd; ++jj) {
     const int j = FWD ? jj : wd - 1 - jj;
-    const double* Sj = S + j * wd;
-    const double xj = T[j] * Sj[j];
-    __syncwarp();
-    if (lane == 0) T[j] = xj;
-    if (FWD ? (lane > j && lane < wd) : (lane < j)) T[lane] = fma(-Sj[lane], xj, T[lane]);
-    __syncwarp();
+    const double a = S[j * wd + lane];   // in bounds: j wd + 31 < 32 x 32
+    const double xj = __shfl_sync(0xffffffffu, t * dl, j);
+    if (FWD ? (lane > j && lane < wd) : (lane < j)) t = fma(-a, xj, t);
   }
-  if (lane < wd) w[st + lane] = T[lane];
+  if (lane < wd) w[st + lane] = t * dl;
+  __syncwarp();
+  if (lane == 0) {
+    fence_acq_rel_gpu();
+    st_relaxed_u32(sp.done + tk.sn, ep);
+  }
+}
+
+// A new solve: both sweeps' tickets from zero, done flags of earlier solves stale.
+__device__ __forceinline__ void sweep_begin(SweepCtl* ctl) {
+  ctl->tick[0] = 0u;
+  ctl->tick[1] = 0u;
+  ctl->epoch += 1u;
 }
 
 // r = F^c_{k+1} - K^c Psi_pred on the permuted rows (a fixed summation order per row)
 __global__ void __launch_bounds__(256) imex_residual_kernel(DevProblem pb, ImexDev im) {
   const unsigned long long k = *((volatile unsigned long long*)pb.step);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sweep_begin(im.ctl);
   double fk1 = 0.0;
   if (pb.f_e > 0.0 && im.Fc) fk1 = ricker_imex((double)(k + 1) * pb.dt, pb.f_e);
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
@@ -181,6 +244,7 @@ __global__ void __launch_bounds__(256) imex_correct_kernel(DevProblem pb, ImexDe
 __global__ void __launch_bounds__(256) imex_gather_kernel(ImexDev im, const double* __restrict__ in,
                                                           const double* __restrict__ scal) {
   const double sc = scal ? *scal : 1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sweep_begin(im.ctl);
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x)
     im.work[r] = in[im.c_dof[im.perm[r]]] * sc;
 }
@@ -192,21 +256,15 @@ __global__ void __launch_bounds__(256) imex_scatter_kernel(ImexDev im, double* _
 
 static int rows_grid(const ImexDev& im) { return (int)std::min<int64_t>((im.n_rows + 255) / 256, 4096); }
 
-// the launches of one triangular solve, height by height (the CTA ranges live on the host)
-static cudaError_t launch_levels(const ImexDev& im, bool fwd, cudaStream_t st) {
-  const int32_t* ptr = fwd ? im.fs.cta_ptr_host : im.bs.cta_ptr_host;
-  for (int hh = 0; hh < im.n_heights; ++hh) {
-    const int h = fwd ? hh : im.n_heights - 1 - hh;
-    const int c0 = ptr[h], n = ptr[h + 1] - ptr[h];
-    if (n <= 0) continue;
-    if (fwd)
-      imex_level_kernel<true><<<n, kLevelThreads, 0, st>>>(im, c0);
-    else
-      imex_level_kernel<false><<<n, kLevelThreads, 0, st>>>(im, c0);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+// one sweep: one CTA per task
+static cudaError_t launch_sweep(const ImexDev& im, bool fwd, cudaStream_t st) {
+  const int n = (fwd ? im.fs : im.bs).n_tasks;
+  if (n <= 0) return cudaSuccess;
+  if (fwd)
+    imex_sweep_kernel<true><<<n, kLevelThreads, 0, st>>>(im);
+  else
+    imex_sweep_kernel<false><<<n, kLevelThreads, 0, st>>>(im);
+  return cudaGetLastError();
 }
 
 // One triangular solve with the Cholesky factor L of S (permuted order), for the power
@@ -218,7 +276,7 @@ cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* s
   if (im.n_rows == 0) return cudaSuccess;
   imex_gather_kernel<<<rows_grid(im), 256, 0, st>>>(im, in, scal);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_levels(im, !backward, st);
+  if (e == cudaSuccess) e = launch_sweep(im, !backward, st);
   if (e != cudaSuccess) return e;
   imex_scatter_kernel<<<rows_grid(im), 256, 0, st>>>(im, out);
   return cudaGetLastError();
@@ -245,8 +303,8 @@ cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* o
   if (im.n_rows == 0) return cudaSuccess;
   imex_residual_kernel<<<rows_grid(im), 256, 0, st>>>(pb, im);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_levels(im, true, st);
-  if (e == cudaSuccess) e = launch_levels(im, false, st);
+  if (e == cudaSuccess) e = launch_sweep(im, true, st);
+  if (e == cudaSuccess) e = launch_sweep(im, false, st);
   if (e != cudaSuccess) return e;
   imex_correct_kernel<<<rows_grid(im), 256, 0, st>>>(pb, im, out);
   return cudaGetLastError();

@@ -179,6 +179,7 @@ void Handle::build_device() {
   pb.done = reinterpret_cast<unsigned int*>(counters + 1);
   pb.flags = reinterpret_cast<int*>(counters + 2);
   pb.tile_counter = reinterpret_cast<int*>(counters + 3);
+  if (imex) imex_dev.flags = pb.flags;
   op_fp64_tiles(s.dim, s.p, s.ncomp, tile);
   for (int k = 0; k < 3; ++k) pb.tiles[k] = k < s.dim ? (s.n[k] + tile[k] - 1) / tile[k] : 1;
   n_blocks = op_fp64_blocks(pb);
@@ -473,38 +474,57 @@ void Handle::imex_upload_factor() {
   const ImexData& I = imex_host;
   const SparseChol& L = I.chol;
   ImexDev& D = imex_dev;
-  D.n_heights = (int)I.gh_sn_ptr.size() - 1;
-  D.fs.cta_ptr_host = I.fsplit.cta_ptr.data();
-  D.bs.cta_ptr_host = I.bsplit.cta_ptr.data();
   size_t nnz = L.Lx.size();
+  const int64_t n_parts = std::max<int64_t>({I.fsplit.n_parts, I.bsplit.n_parts, 32});
   if (imex_nnz_alloc != nnz) {
-    // the pattern, the order and the supernodes do not depend on dt: allocated once
+    // the pattern, the order, the supernodes and the work split do not depend on dt:
+    // uploaded once (32-bit column indices and entry offsets)
+    if (nnz > (size_t)INT32_MAX || I.n_c > (int64_t)INT32_MAX)
+      throw std::runtime_error("IMEX factor too large for 32-bit indices");
     const size_t nd = I.sn_D.size();
-    D.Lp = static_cast<int64_t*>(dalloc((I.n_c + 1) * sizeof(int64_t)));
-    D.Li = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t)));
-    D.Lx = static_cast<double*>(dalloc(nnz * sizeof(double)));
-    D.Up = static_cast<int64_t*>(dalloc((I.n_c + 1) * sizeof(int64_t)));
-    D.Ui = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t)));
-    D.Ux = static_cast<double*>(dalloc(nnz * sizeof(double)));
+    std::vector<int32_t> li(std::max<size_t>(nnz, 1), 0), ui(li.size(), 0);
+    for (size_t k = 0; k < nnz; ++k) {
+      li[k] = (int32_t)L.Li[k];
+      ui[k] = (int32_t)L.Ui[k];
+    }
+    D.Li = upload(li);
+    D.Ui = upload(ui);
+    D.Lx = static_cast<double*>(dalloc(std::max<size_t>(nnz, 1) * sizeof(double)));
+    D.Ux = static_cast<double*>(dalloc(std::max<size_t>(nnz, 1) * sizeof(double)));
     D.D = static_cast<double*>(dalloc(std::max<size_t>(nd, 1) * sizeof(double)));
     D.DT = static_cast<double*>(dalloc(std::max<size_t>(nd, 1) * sizeof(double)));
-    D.sn_start = upload(I.sn_start);
-    D.sn_w = upload(I.sn_size);
-    D.sn_doff = upload(I.sn_doff);
+    // one task per CTA of each sweep, in ticket order
+    const size_t nsn = I.sn_start.size();
     for (int dir = 0; dir < 2; ++dir) {
       const ImexSplit& sp = dir == 0 ? I.fsplit : I.bsplit;
+      std::vector<LevelTask> t;
+      for (const int32_t q : sp.order)
+        for (int32_t c = 0; c < sp.g[q]; ++c) {
+          LevelTask e{};
+          e.st = (int32_t)I.sn_start[q];
+          e.wd_tpr = I.sn_size[q] | (sp.tpr[q] << 16);
+          e.c = c;
+          e.g = sp.g[q];
+          e.doff = I.sn_doff[q];
+          e.pbase = sp.pbase[q];
+          e.sn = q;
+          e.dep_beg = sp.dep_ptr[q];
+          e.dep_n = sp.dep_ptr[q + 1] - sp.dep_ptr[q];
+          t.push_back(e);
+        }
       ImexSplitDev& sd = dir == 0 ? D.fs : D.bs;
-      sd.cta = reinterpret_cast<const int2*>(upload(sp.cta));
-      sd.g = upload(sp.g);
-      sd.lpr = upload(sp.lpr);
-      sd.pbase = upload(sp.pbase);
+      sd.n_tasks = (int)t.size();
+      sd.task = upload(t);
+      sd.dep = upload(sp.dep);
+      sd.done = static_cast<unsigned int*>(dalloc(std::max<size_t>(nsn, 1) * sizeof(unsigned int)));
+      check(cudaMemsetAsync(sd.done, 0, std::max<size_t>(nsn, 1) * sizeof(unsigned int), stream), "memset");
     }
-    D.part = static_cast<double*>(dalloc(std::max<int64_t>({I.fsplit.n_parts, I.bsplit.n_parts, 1}) * sizeof(double)));
-    D.cnt = static_cast<unsigned int*>(dalloc(std::max<size_t>(I.sn_start.size(), 1) * sizeof(unsigned int)));
-    check(cudaMemsetAsync(D.cnt, 0, std::max<size_t>(I.sn_start.size(), 1) * sizeof(unsigned int), stream), "memset");
+    D.ctl = static_cast<SweepCtl*>(dalloc(sizeof(SweepCtl)));
+    check(cudaMemsetAsync(D.ctl, 0, sizeof(SweepCtl), stream), "memset");
+    D.part = static_cast<double*>(dalloc(n_parts * sizeof(double)));
+    D.cnt = static_cast<unsigned int*>(dalloc((n_parts / 32) * sizeof(unsigned int)));
     // one 8-byte descriptor per row (its off-block entry range), so that a row costs one
-    // load before its entries (the pattern does not depend on dt)
-    if (nnz > (size_t)INT32_MAX) throw std::runtime_error("IMEX factor too large for 32-bit entry offsets");
+    // load before its entries
     std::vector<int32_t> fd(2 * std::max<int64_t>(I.n_c, 1), 0), bd(fd.size(), 0);
     for (int64_t r = 0; r < I.n_c; ++r) {
       fd[2 * r] = (int32_t)L.Lp[r];
@@ -519,15 +539,11 @@ void Handle::imex_upload_factor() {
   auto cp = [&](const void* dst, const void* src, size_t bytes) {
     if (bytes) check(cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, stream), "factor upload");
   };
-  cp(D.Lp, L.Lp.data(), L.Lp.size() * sizeof(int64_t));
-  cp(D.Li, L.Li.data(), nnz * sizeof(int64_t));
   cp(D.Lx, L.Lx.data(), nnz * sizeof(double));
-  cp(D.Up, L.Up.data(), L.Up.size() * sizeof(int64_t));
-  cp(D.Ui, L.Ui.data(), nnz * sizeof(int64_t));
   cp(D.Ux, L.Ux.data(), nnz * sizeof(double));
   cp(D.D, I.sn_D.data(), I.sn_D.size() * sizeof(double));
-  check(cudaMemsetAsync(D.cnt, 0, std::max<size_t>(I.sn_start.size(), 1) * sizeof(unsigned int), stream), "memset");
   cp(D.DT, I.sn_DT.data(), I.sn_DT.size() * sizeof(double));
+  check(cudaMemsetAsync(D.cnt, 0, (n_parts / 32) * sizeof(unsigned int), stream), "memset");
   check(cudaStreamSynchronize(stream), "factor upload");
 }
 
@@ -1221,7 +1237,7 @@ int ibfem_sync(ibfem_t* h) {
   check(cudaStreamSynchronize(h->stream), "sync");
   int flags = 0;
   check(cudaMemcpy(&flags, h->dev.flags, sizeof(int), cudaMemcpyDeviceToHost), "flags");
-  if (flags & 2) return fail(IBFEM_ERR_TIMEOUT, "a bounded tensor-core wait gave up (results of that step are invalid)");
+  if (flags & 2) return fail(IBFEM_ERR_TIMEOUT, "a bounded device wait gave up (results of that step are invalid)");
   if (flags & 1) return fail(IBFEM_ERR_DIVERGED, "non-finite value in the state");
   return IBFEM_OK;
   IBFEM_CATCH
@@ -1254,7 +1270,7 @@ int ibfem_sample(ibfem_t* h, int64_t max_rows, double* out, int64_t* rows) {
   *rows = r;
   int flags = 0;
   check(cudaMemcpy(&flags, h->dev.flags, sizeof(int), cudaMemcpyDeviceToHost), "flags");
-  if (flags & 2) return fail(IBFEM_ERR_TIMEOUT, "a bounded tensor-core wait gave up (results of that step are invalid)");
+  if (flags & 2) return fail(IBFEM_ERR_TIMEOUT, "a bounded device wait gave up (results of that step are invalid)");
   if (flags & 1) return fail(IBFEM_ERR_DIVERGED, "non-finite value in the state");
   return IBFEM_OK;
   IBFEM_CATCH
