@@ -180,13 +180,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
+def run_serving(args, rate=None):
     """Continuous batching of a seeded Poisson stream of mixed 2D/3D requests through the
     batched exact tensor-core path; returns the latency / throughput summary."""
     from paper_2501_19013_gb300 import workloads as W
     from paper_2501_19013_gb300.serve import Request, Server, TcBackend
     n = args.serve_requests
-    arr = W.poisson_arrivals(n, args.serve_rate, seed=0)
+    rate = args.serve_rate if rate is None else rate
+    arr = W.poisson_arrivals(n, rate, seed=0)
     reqs = []
     for i in range(n):
         w = W.serving_request(i)
@@ -197,7 +198,7 @@ def run_serving(args):
     st = srv.run(reqs)
     be.close()
     out = st.summary()
-    out.update({"rate_per_s": args.serve_rate, "hbm_budget_gb": args.serve_budget_gb,
+    out.update({"rate_per_s": rate, "hbm_budget_gb": args.serve_budget_gb,
                 "slots": args.serve_slots, "precision": "exact",
                 "mix": "seeded: 70% 2D plates 32^2-256^2 p2-4 scalar/plane strain with 1-12 holes, "
                        "30% 3D porous cubes 16^3-48^3 p2-3; 500-5000 steps; dt = 0.9 dt_crit each",
@@ -250,9 +251,9 @@ def run_multi_source(args, w, r):
 
 def parse_variant(v, w):
     """'fp64' | 'exact' | 'exact64' | 'bf16x3' | 'bf16' -> CDM with the workload's
-    stabilisation; 'imex[:exact64]' -> Newmark IMEX (its explicit part by the FP64 or the
-    FP64-grade tensor-core kernel); 'cons[:exact64]' -> CDM with the consistent cut mass;
-    'ms:<precision>' -> CDM with mass scaling."""
+    stabilisation; 'imex[:exact64|:exact]' -> Newmark IMEX (its explicit part by the FP64, the
+    FP64-grade or the exact tensor-core kernel); 'cons[:exact64|:exact]' -> CDM with the
+    consistent cut mass; 'ms:<precision>' -> CDM with mass scaling."""
     if v.split(":")[0] == "imex":
         return w.with_(scheme="imex", stab="none"), (v.split(":")[1] if ":" in v else "fp64")
     if v.split(":")[0] == "cons":
@@ -277,10 +278,11 @@ def accuracy_against_fp64(results):
     L2 error of the final field (``rel_l2``) and the paper's observer error (Eq. error:
     e_100 and e_N over all N steps, ``e_obs``); None where there is no comparable FP64 run."""
     from paper_2501_19013_gb300.metrics import observer_errors
-    ref = results.get("fp64")
+    refs = {(r["scheme"], r["stab"]): r for r in results.values() if int(r["info"].precision) == 0}
     for r in results.values():
         r["rel_l2"], r["e_obs"] = None, None
-        if ref is None or r["scheme"] != "cdm" or r["stab"] != ref["stab"]:
+        ref = refs.get((r["scheme"], r["stab"]))
+        if ref is None:
             continue
         nr = np.linalg.norm(ref["u_end"])
         r["rel_l2"] = float(np.linalg.norm(r["u_end"] - ref["u_end"]) / nr) if nr > 0 else 0.0
@@ -567,6 +569,14 @@ def run_ours(args, rank, world, local_rank):
         r["solver"].close()
     if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = run_serving(args)
+        # the same request stream arriving faster: latency and aggregate throughput under load
+        loads = []
+        for rate in [float(x) for x in args.serve_load_rates.split(",") if x.strip()]:
+            o = run_serving(args, rate)
+            loads.append({k: o.get(k) for k in ("rate_per_s", "completed", "failed", "p50_s", "p99_s",
+                                                 "dof_steps_per_s", "max_concurrent", "p50_stage_s")})
+        if loads:
+            line["serving_under_load"] = loads
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -590,6 +600,8 @@ def main():
                     help="loads of the shared-geometry multi-source run (0: none)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving run (0: none)")
     ap.add_argument("--serve-rate", type=float, default=8.0, help="Poisson arrival rate of the serving run (1/s)")
+    ap.add_argument("--serve-load-rates", default="16,32",
+                    help="further arrival rates (1/s) of the same requests, reported under serving_under_load")
     ap.add_argument("--serve-slots", type=int, default=32, help="maximum concurrent members of the batch")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="device memory budget of the serving run")
     ap.add_argument("--workload", default="plate_holes_elastic",

@@ -69,7 +69,9 @@ enum { IBFEM_SCALAR = 0, IBFEM_ELASTIC_PLANE_STRAIN = 1 };
  * IBFEM_CDM_CONSISTENT, the central-difference method with the consistent mass of the cut
  * cells (the paper's "SCM con." CDM): Algorithm 2 with beta = 0, i.e. the DOFs of cut cells
  * are advanced explicitly through a solve with their consistent (EVS-stabilised when
- * eps > 0) mass block M^cc. */
+ * eps > 0) mass block M^cc.  IMEX and the consistent-mass CDM take precision IBFEM_FP64,
+ * IBFEM_EXACT64_TC or IBFEM_EXACT_TC (the explicit part on that kernel; the solves are
+ * FP64); ibfem_create returns IBFEM_ERR_ARG for the others. */
 enum { IBFEM_CDM = 0, IBFEM_IMEX = 1, IBFEM_CDM_CONSISTENT = 2 };
 /* Precision of the element contractions.  The integrator state (u^k, u^{k-1}), the
  * central-difference update, the IMEX solves and the power iteration are FP64 always. */
@@ -120,7 +122,7 @@ typedef struct {
     double rho, c;            /* density, wave speed (scalar)                          */
     double E, nu;             /* Young's modulus, Poisson ratio (elastic)              */
     int scheme;               /* IBFEM_CDM, IBFEM_IMEX or IBFEM_CDM_CONSISTENT         */
-    int precision;            /* IBFEM_FP64 / _EXACT_TC / _BF16X3_TC / _BF16_TC         */
+    int precision;            /* IBFEM_FP64 / _EXACT_TC / _BF16X3_TC / _BF16_TC / _EXACT64_TC */
     void* stream;             /* cudaStream_t to run on, NULL = the legacy stream      */
     void* (*dev_alloc)(size_t bytes, void* ctx);  /* optional device allocator         */
     void (*dev_free)(void* ptr, void* ctx);

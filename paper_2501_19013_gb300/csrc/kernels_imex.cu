@@ -5,13 +5,14 @@
 // (and Psi'_pred^c) into the new state buffer:
 //   * imex_cell_apply : y_e = K^e x_e for every cell touching a c-DOF (one warp per cell,
 //                       FP64), x = [Psi_{k+1}^d ; Psi_pred^c];
-//   * imex_solve      : the residual r = F^c_{k+1} - K^c Psi_pred gathered in a fixed
-//                       order, the forward and backward solves with the host Cholesky
-//                       factor of S = M^cc + beta dt^2 K^cc by supernode blocks (one
-//                       dependency-driven launch per sweep), and the Newmark correction
+//   * imex_solve      : the forward and backward solves with the host Cholesky factor of
+//                       S = M^cc + beta dt^2 K^cc by supernode blocks, one dependency-
+//                       driven launch per sweep; the forward sweep forms the residual
+//                       r = F^c_{k+1} - K^c Psi_pred of its rows (gathered in a fixed
+//                       order), the backward sweep applies the Newmark correction
 //                       Psi''^c = S^{-1} r, Psi'^c = Psi'_pred^c + gamma dt Psi''^c,
-//                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c, which advances the step
-//                       counter.
+//                       Psi^c = Psi_pred^c + beta dt^2 Psi''^c to its rows and advances the
+//                       step counter.
 #include <algorithm>
 
 #include "internal.h"
@@ -25,11 +26,19 @@ __device__ __forceinline__ double ricker_imex(double t, double f_e) {
   return (1.0 - 2.0 * q * q) * exp(-q * q);
 }
 
+// A new solve: both sweeps' tickets from zero, done flags of earlier solves stale.
+__device__ __forceinline__ void sweep_begin(SweepCtl* ctl) {
+  ctl->tick[0] = 0u;
+  ctl->tick[1] = 0u;
+  ctl->epoch += 1u;
+}
+
 template <int DIM, int P, int NC>
 __global__ void __launch_bounds__(256) imex_cell_apply_kernel(DevProblem pb, ImexDev im, const double* __restrict__ x) {
   constexpr int NN1 = P + 1;
   constexpr int NL = (DIM == 2 ? NN1 * NN1 : NN1 * NN1 * NN1) * NC;
   __shared__ double xs[8][NL];
+  if (blockIdx.x == 0 && threadIdx.x == 0) sweep_begin(im.ctl);   // the solve follows
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int slot = blockIdx.x * 8 + warp;
   if (slot >= im.n_cells) return;
@@ -86,14 +95,26 @@ __device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
   return v;
 }
 
-__device__ __forceinline__ void st_relaxed_u32(unsigned int* p, unsigned int v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// atomic add with release (this CTA's partial sums, ordered before it by the block barrier)
+// and acquire (the other CTAs' partial sums, for the last to arrive) semantics
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
 }
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-template <bool FWD>
-__global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(ImexDev im) {
+// STEP: the sweeps of an IMEX step: the forward sweep forms its rows' right-hand sides, the
+// residual r = F^c_{k+1} - K^c Psi_pred (a fixed order per row), and the backward sweep
+// applies the Newmark correction to its rows (and advances the step counter once); else
+// the right-hand side is the work vector and the solution stays there.
+template <bool FWD, bool STEP>
+__global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(DevProblem pb, ImexDev im, double* __restrict__ out) {
   __shared__ double S[kSnMax * kSnMax];
   __shared__ double T[kSnMax];
   __shared__ int ticket, last;
@@ -113,24 +134,37 @@ __global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(ImexDev im) {
   // and the first round of this thread's entries
   const double* __restrict__ M = (FWD ? im.DT : im.D) + tk.doff;
   for (int e = threadIdx.x; e < wd * wd; e += kLevelThreads) S[e] = M[e];
-  const double rhs = threadIdx.x < wd ? __ldcg(w + st + threadIdx.x) : 0.0;
+  double rhs = 0.0;
+  if (threadIdx.x < wd) {
+    if (STEP && FWD) {
+      const int64_t r = st + threadIdx.x;
+      const unsigned long long k = *((volatile unsigned long long*)pb.step);
+      const double fk1 = pb.f_e > 0.0 && im.Fc ? ricker_imex((double)(k + 1) * pb.dt, pb.f_e) : 0.0;
+      double acc = im.Fc ? im.Fc[r] * fk1 : 0.0;
+      for (int64_t e = im.g_ptr[r]; e < im.g_ptr[r + 1]; ++e) acc -= im.Y[im.g_idx[e]];
+      rhs = acc;
+    } else {
+      rhs = __ldcg(w + st + threadIdx.x);
+    }
+  }
+  if (STEP && !FWD && ticket == 0 && threadIdx.x == 0) *pb.step += 1ull;
   const int32_t* __restrict__ I = FWD ? im.Li : im.Ui;
   const double* __restrict__ X = FWD ? im.Lx : im.Ux;
   const int row = threadIdx.x / tpr, sub = threadIdx.x & (tpr - 1);
-  int pb = 0, pe = 0;
+  int e0 = 0, e1 = 0;   // this thread's row share: entries [e0, e1)
   if (row < wd) {
     const int2 d = (FWD ? im.row_fdesc : im.row_bdesc)[st + row];
     const int len = d.y - d.x;
-    pb = d.x + (int)((int64_t)len * c / g);
-    pe = d.x + (int)((int64_t)len * (c + 1) / g);
+    e0 = d.x + (int)((int64_t)len * c / g);
+    e1 = d.x + (int)((int64_t)len * (c + 1) / g);
   }
   double xv[kSweepK];
   int iv[kSweepK];
 #pragma unroll
   for (int k = 0; k < kSweepK; ++k) {
-    const int p = pb + sub + k * tpr;
-    xv[k] = p < pe ? X[p] : 0.0;
-    iv[k] = p < pe ? I[p] : -1;
+    const int p = e0 + sub + k * tpr;
+    xv[k] = p < e1 ? X[p] : 0.0;
+    iv[k] = p < e1 ? I[p] : -1;
   }
   // the supernodes this one reads: relaxed polls, one acquire fence once they are done
   bool waited = false;
@@ -153,22 +187,16 @@ __global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(ImexDev im) {
 #pragma unroll
   for (int k = 0; k < kSweepK; ++k)
     if (iv[k] >= 0) acc = fma(xv[k], __ldcg(w + iv[k]), acc);
-  for (int p = pb + sub + kSweepK * tpr; p < pe; p += tpr) acc = fma(X[p], __ldcg(w + I[p]), acc);
+  for (int p = e0 + sub + kSweepK * tpr; p < e1; p += tpr) acc = fma(X[p], __ldcg(w + I[p]), acc);
   for (int o = tpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, tpr);
   if (g == 1) {
     if (sub == 0 && row < wd) T[row] = acc;
   } else {
     // (2) partial sums; the last CTA of the supernode takes over
-    if (sub == 0 && row < wd) {
-      im.part[tk.pbase + (int64_t)c * kSnMax + row] = acc;
-      fence_acq_rel_gpu();
-    }
+    if (sub == 0 && row < wd) im.part[tk.pbase + (int64_t)c * kSnMax + row] = acc;
     __syncthreads();
     unsigned int* cnt = im.cnt + (tk.pbase >> 5);
-    if (threadIdx.x == 0) {
-      last = atomicAdd(cnt, 1u) == (unsigned)(g - 1);
-      if (last) fence_acq_rel_gpu();
-    }
+    if (threadIdx.x == 0) last = atom_add_acq_rel_u32(cnt, 1u) == (unsigned)(g - 1);
     __syncthreads();
     if (!last) return;
     // 8 threads per row, each over every 8th share in order, then a fixed shuffle tree
@@ -194,51 +222,23 @@ __global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(ImexDev im) {
     const double xj = __shfl_sync(0xffffffffu, t * dl, j);
     if (FWD ? (lane > j && lane < wd) : (lane < j)) t = fma(-a, xj, t);
   }
-  if (lane < wd) w[st + lane] = t * dl;
-  __syncwarp();
-  if (lane == 0) {
-    fence_acq_rel_gpu();
-    st_relaxed_u32(sp.done + tk.sn, ep);
-  }
-}
-
-// A new solve: both sweeps' tickets from zero, done flags of earlier solves stale.
-__device__ __forceinline__ void sweep_begin(SweepCtl* ctl) {
-  ctl->tick[0] = 0u;
-  ctl->tick[1] = 0u;
-  ctl->epoch += 1u;
-}
-
-// r = F^c_{k+1} - K^c Psi_pred on the permuted rows (a fixed summation order per row)
-__global__ void __launch_bounds__(256) imex_residual_kernel(DevProblem pb, ImexDev im) {
-  const unsigned long long k = *((volatile unsigned long long*)pb.step);
-  if (blockIdx.x == 0 && threadIdx.x == 0) sweep_begin(im.ctl);
-  double fk1 = 0.0;
-  if (pb.f_e > 0.0 && im.Fc) fk1 = ricker_imex((double)(k + 1) * pb.dt, pb.f_e);
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc = im.Fc ? im.Fc[r] * fk1 : 0.0;
-    for (int64_t e = im.g_ptr[r]; e < im.g_ptr[r + 1]; ++e) acc -= im.Y[im.g_idx[e]];
-    im.work[r] = acc;
-  }
-}
-
-// Newmark correction on the c-DOFs: Psi''^c = S^{-1} r (in work), Psi'^c += gamma dt Psi''^c,
-// Psi^c = Psi_pred^c + beta dt^2 Psi''^c; one thread advances the step counter
-__global__ void __launch_bounds__(256) imex_correct_kernel(DevProblem pb, ImexDev im, double* __restrict__ out) {
-  bool bad = false;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < im.n_rows; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ci = im.perm[r];
-    const double a = im.work[r];
-    im.ac[ci] = a;
-    im.vc[ci] = fma(im.gamma_dt, a, im.vc[ci]);
+  const double x = t * dl;
+  if (lane < wd) w[st + lane] = x;
+  if (STEP && !FWD && lane < wd) {
+    // Newmark correction of Algorithm 2 on this row: Psi''^c = x, Psi'^c += gamma dt x,
+    // Psi^c = Psi_pred^c + beta dt^2 x
+    const int64_t ci = im.perm[st + lane];
+    im.ac[ci] = x;
+    im.vc[ci] = fma(im.gamma_dt, x, im.vc[ci]);
     const int64_t dof = im.c_dof[ci];
-    const double nv = fma(im.beta_dt2, a, out[dof]);
+    const double nv = fma(im.beta_dt2, x, out[dof]);
     out[dof] = nv;
-    if (!isfinite(nv)) bad = true;
+    if (!isfinite(nv)) atomicOr(pb.flags, 1);
   }
-  if (bad) atomicOr(pb.flags, 1);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *pb.step += 1ull;
+  __syncwarp();
+  if (lane == 0) st_release_u32(sp.done + tk.sn, ep);
 }
+
 
 // gather b[r] = in[c_dof[perm[r]]] * scal into work, or scatter out[c_dof[perm[r]]] = work[r]
 __global__ void __launch_bounds__(256) imex_gather_kernel(ImexDev im, const double* __restrict__ in,
@@ -257,13 +257,16 @@ __global__ void __launch_bounds__(256) imex_scatter_kernel(ImexDev im, double* _
 static int rows_grid(const ImexDev& im) { return (int)std::min<int64_t>((im.n_rows + 255) / 256, 4096); }
 
 // one sweep: one CTA per task
-static cudaError_t launch_sweep(const ImexDev& im, bool fwd, cudaStream_t st) {
+template <bool STEP>
+static cudaError_t launch_sweep(const DevProblem* pb, const ImexDev& im, double* out, bool fwd, cudaStream_t st) {
   const int n = (fwd ? im.fs : im.bs).n_tasks;
   if (n <= 0) return cudaSuccess;
+  const DevProblem none{};
+  const DevProblem& p = pb ? *pb : none;
   if (fwd)
-    imex_sweep_kernel<true><<<n, kLevelThreads, 0, st>>>(im);
+    imex_sweep_kernel<true, STEP><<<n, kLevelThreads, 0, st>>>(p, im, out);
   else
-    imex_sweep_kernel<false><<<n, kLevelThreads, 0, st>>>(im);
+    imex_sweep_kernel<false, STEP><<<n, kLevelThreads, 0, st>>>(p, im, out);
   return cudaGetLastError();
 }
 
@@ -276,7 +279,7 @@ cudaError_t launch_imex_tri(const ImexDev& im, const double* in, const double* s
   if (im.n_rows == 0) return cudaSuccess;
   imex_gather_kernel<<<rows_grid(im), 256, 0, st>>>(im, in, scal);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_sweep(im, !backward, st);
+  if (e == cudaSuccess) e = launch_sweep<false>(nullptr, im, nullptr, !backward, st);
   if (e != cudaSuccess) return e;
   imex_scatter_kernel<<<rows_grid(im), 256, 0, st>>>(im, out);
   return cudaGetLastError();
@@ -301,13 +304,9 @@ cudaError_t launch_imex_cell_apply(const DevProblem& pb, const ImexDev& im, cons
 
 cudaError_t launch_imex_solve(const DevProblem& pb, const ImexDev& im, double* out, cudaStream_t st) {
   if (im.n_rows == 0) return cudaSuccess;
-  imex_residual_kernel<<<rows_grid(im), 256, 0, st>>>(pb, im);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_sweep(im, true, st);
-  if (e == cudaSuccess) e = launch_sweep(im, false, st);
-  if (e != cudaSuccess) return e;
-  imex_correct_kernel<<<rows_grid(im), 256, 0, st>>>(pb, im, out);
-  return cudaGetLastError();
+  cudaError_t e = launch_sweep<true>(&pb, im, out, true, st);
+  if (e == cudaSuccess) e = launch_sweep<true>(&pb, im, out, false, st);
+  return e;
 }
 
 }  // namespace ibfem

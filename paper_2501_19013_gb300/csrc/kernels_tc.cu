@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
     off[j] = j < NL ? ((c * PY + b) * PX + a) * NC + comp : -1;
   }
   unsigned long long k = 0;
-  if (!BATCH && mode == kModeCDM) k = *((volatile unsigned long long*)pb.step);
+  if (!BATCH && (mode == kModeCDM || mode == kModeImex)) k = *((volatile unsigned long long*)pb.step);
   if (!BATCH && blockIdx.x == 0 && mode == kModeCDM && pb.n_obs_rows > 0 && pb.ring_cap > 0) {
     for (int r = tid; r < pb.n_obs_rows; r += blockDim.x) {
       double acc = 0.0;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
     }
   }
   double fk = 0.0;
-  if (!BATCH && (mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0)
+  if (!BATCH && (mode == kModeCDM || mode == kModeStartup || mode == kModeImex) && pb.tsrc_ptr && pb.f_e > 0.0)
     fk = ricker_tc((double)k * pb.dt, pb.f_e);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
     // The cells of a node are summed in the order (z, y, x) of their offsets, lower first.
     const int ox0 = X0 * P, oy0 = Y0 * P, oz0 = DIM == 3 ? Z0 * P : 0;
     int src_lo = 0, src_hi = 0;
-    if ((mode == kModeCDM || mode == kModeStartup) && pb.tsrc_ptr && pb.f_e > 0.0) {
+    if ((mode == kModeCDM || mode == kModeStartup || mode == kModeImex) && pb.tsrc_ptr && pb.f_e > 0.0) {
       src_lo = pb.tsrc_ptr[tile];
       src_hi = pb.tsrc_ptr[tile + 1];
     }
@@ -693,12 +693,25 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
         out[dof] = f32_to_f64_scaled(sh, 0) + f32_to_f64_scaled(se + lo, 0);
         return;
       }
-      if (!(mh > 0.f)) return;
+      if (!(mh > 0.f)) {
+        // IMEX mode, a c-DOF (dt^2/m = -(c + 1) in FP64, no FP32 slices): the Newmark
+        // predictor of Algorithm 2 (its K u is taken by the c-set solve)
+        if (mode == kModeImex) {
+          const double mi = pb.minv[dof];
+          if (mi < 0.0) {
+            const int64_t ci = (int64_t)(-mi) - 1;
+            const double a = pb.imex_ac[ci], v = pb.imex_vc[ci];
+            out[dof] = uval + pb.dt * v + pb.imex_c1 * a;
+            pb.imex_vc[ci] = v + pb.imex_c2 * a;
+          }
+        }
+        return;
+      }
       const float r = -(sh + (se + lo));   // -K u rounded once to FP32 (the load follows below)
       const float d32 = fmaf(mh, r, ml * r);
       if (!isfinite(d32)) bad = true;
       const double delta = f32_to_f64_scaled(d32, 0);
-      if (mode == kModeCDM)
+      if (mode == kModeCDM || mode == kModeImex)
         out[dof] = fma(2.0, uval, -upv) + delta;
       else
         out[dof] = uval - pb.dt * upv + 0.5 * delta;
@@ -818,7 +831,7 @@ __global__ void __launch_bounds__(256, 2) op_tc_kernel(const __grid_constant__ D
     // FP64: u^{k+1} += (dt^2 / m) F_k (start-up step: half of it)
     if (src_lo < src_hi && mode != kModeApply) {
       __syncthreads();   // this tile's updates of `out` are visible to every thread
-      const double w = mode == kModeCDM ? 1.0 : 0.5;
+      const double w = mode == kModeStartup ? 0.5 : 1.0;
       for (int s2 = src_lo + tid; s2 < src_hi; s2 += blockDim.x) {
         const int64_t dof = pb.tsrc_dof[s2];
         const double mi = pb.minv[dof];

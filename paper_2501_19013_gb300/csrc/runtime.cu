@@ -608,7 +608,7 @@ void Handle::enqueue_step(int cur) {
     if (timing) step_last_ev.push_back(ev_used - 1);
     return;
   }
-  if (opt.precision != IBFEM_FP64 && opt.precision != IBFEM_EXACT64_TC) {
+  if (opt.precision != IBFEM_FP64 && opt.precision != IBFEM_EXACT64_TC && !imex) {
     slot_name[1] = tc_scheme() == 0 ? "op_tc_exact_fused_cdm" : (tc_scheme() == 1 ? "op_tc_bf16x3_fused_cdm" : "op_tc_bf16_fused_cdm");
     if (timing) step_first_ev.push_back(ev_used);
     timed_begin(1);
@@ -618,12 +618,14 @@ void Handle::enqueue_step(int cur) {
     return;
   }
   if (imex) {
-    // Algorithm 2: the explicit part (d-DOF update and c-DOF predictor) by the FP64 kernel or
-    // by the FP64-grade tensor-core kernel, then the c-cells' products and the c-set solve
-    const bool tc = opt.precision == IBFEM_EXACT64_TC;
+    // Algorithm 2: the explicit part (d-DOF update and c-DOF predictor) by the FP64 kernel,
+    // the FP64-grade or the exact tensor-core kernel, then the c-cells' products and the
+    // c-set solve
+    const bool tc64 = opt.precision == IBFEM_EXACT64_TC, tc = opt.precision == IBFEM_EXACT_TC;
     OpInput x{U[cur], nullptr, nullptr};
     slot_name[1] = "observers";
-    slot_name[2] = tc ? "op_tc_exact64_fused_imex_explicit" : "op_fp64_fused_imex_explicit";
+    slot_name[2] = tc64 ? "op_tc_exact64_fused_imex_explicit"
+                        : (tc ? "op_tc_exact_fused_imex_explicit" : "op_fp64_fused_imex_explicit");
     slot_name[3] = "imex_cell_apply";
     slot_name[4] = "imex_solve";
     if (timing) step_first_ev.push_back(ev_used);
@@ -631,8 +633,10 @@ void Handle::enqueue_step(int cur) {
     check(launch_cut_apply_fp64(dev, x, true, stream, false), "observers");
     timed_end();
     timed_begin(2);
-    if (tc)
+    if (tc64)
       check(launch_op_tc64(dev, U[cur], U[1 - cur], kModeImex, stream), "op_tc64_imex");
+    else if (tc)
+      check(launch_op_tc(dev, U[cur], U[1 - cur], kModeImex, tc_scheme(), tc_variant, stream, tc_ctas), "op_tc_imex");
     else
       check(launch_op_fp64(dev, x, U[1 - cur], kModeImex, nullptr, stream), "op_imex");
     timed_end();
@@ -776,8 +780,10 @@ int ibfem_create(const ibfem_grid* grid, int p, const ibfem_geometry* geometry, 
     throw std::invalid_argument("unknown physics");
   if (o.scheme != IBFEM_CDM && o.scheme != IBFEM_IMEX && o.scheme != IBFEM_CDM_CONSISTENT)
     throw std::invalid_argument("unknown scheme");
-  if (o.scheme != IBFEM_CDM && o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT64_TC)
-    throw std::invalid_argument("IMEX and the consistent-mass CDM run at FP64 grade (precision IBFEM_FP64 or IBFEM_EXACT64_TC)");
+  if (o.scheme != IBFEM_CDM && o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT64_TC &&
+      o.precision != IBFEM_EXACT_TC)
+    throw std::invalid_argument(
+        "IMEX and the consistent-mass CDM take precision IBFEM_FP64, IBFEM_EXACT64_TC or IBFEM_EXACT_TC");
   in.need_consistent_mass = o.scheme != IBFEM_CDM;
   if (o.precision != IBFEM_FP64 && o.precision != IBFEM_EXACT_TC && o.precision != IBFEM_BF16X3_TC &&
       o.precision != IBFEM_BF16_TC && o.precision != IBFEM_EXACT64_TC)

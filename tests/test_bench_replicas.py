@@ -46,20 +46,25 @@ def test_single_rank_aggregation():
 
 def test_accuracy_against_fp64_on_fake_runs():
     """The bench's accuracy table: final-field rel-L2 and the observer error e_100 / e_N
-    of each comparable variant against the FP64 path; none for another scheme."""
+    of each variant against the FP64 path of the same scheme and stabilisation; none where
+    that scheme has no FP64 run."""
     import numpy as np
     import bench
 
     class Info:
         ncomp = 2
 
+        def __init__(self, precision):
+            self.precision = precision
+
     t = np.linspace(0.0, 1.0, 1001)
     ref = np.stack([np.sin(5 * t + i) for i in range(6)], axis=1)
     u = np.linspace(1.0, 2.0, 50)
     results = {
-        "fp64": dict(scheme="cdm", stab="evs", u_end=u, series=ref, info=Info()),
-        "exact": dict(scheme="cdm", stab="evs", u_end=u * (1 + 3e-6), series=ref * (1 + 2e-6), info=Info()),
-        "imex": dict(scheme="imex", stab="none", u_end=u, series=ref, info=Info()),
+        "fp64": dict(scheme="cdm", stab="evs", u_end=u, series=ref, info=Info(0)),
+        "exact": dict(scheme="cdm", stab="evs", u_end=u * (1 + 3e-6), series=ref * (1 + 2e-6), info=Info(1)),
+        "imex:exact": dict(scheme="imex", stab="none", u_end=u * (1 - 5e-6), series=ref, info=Info(1)),
+        "cons:exact": dict(scheme="cdm_consistent", stab="evs", u_end=u, series=ref, info=Info(1)),
     }
     bench.accuracy_against_fp64(results)
     assert results["fp64"]["rel_l2"] == 0.0 and results["fp64"]["e_obs"]["e_100"] == 0.0
@@ -69,7 +74,13 @@ def test_accuracy_against_fp64_on_fake_runs():
     assert results["exact"]["e_obs"]["e_N"] == results["exact"]["e_obs"]["e_1000"]
     assert results["exact"]["e_obs"]["observers_left_out"] == 0
     assert len(results["exact"]["e_obs"]["e_1000_per_observer"]) == 3
-    assert results["imex"]["rel_l2"] is None and results["imex"]["e_obs"] is None
+    # no FP64 run of IMEX or of the consistent mass: nothing to compare with
+    assert results["imex:exact"]["rel_l2"] is None and results["imex:exact"]["e_obs"] is None
+    assert results["cons:exact"]["rel_l2"] is None
+    results["imex"] = dict(scheme="imex", stab="none", u_end=u, series=ref, info=Info(0))
+    bench.accuracy_against_fp64(results)
+    assert abs(results["imex:exact"]["rel_l2"] - 5e-6) < 1e-12
+    assert results["imex:exact"]["e_obs"]["e_N"] == 0.0
     del results["fp64"]
     bench.accuracy_against_fp64(results)
     assert results["exact"]["rel_l2"] is None
