@@ -406,6 +406,22 @@ int ibfem_batch_destroy(ibfem_batch_t* b);
  * Errors: ARG (polls outside [1, 2^24]), STATE (host-only handle), CUDA (launch). */
 int ibfem_check_bounded_wait(ibfem_t* h, int polls);
 
+/* Host check of the schedule of the GPU's block triangular solves (the c-set solve of
+ * Algorithm 2, Sec. 2.6, and of the consistent-mass CDM): factors S = M^cc + beta_dt2 K^cc
+ * on the host (a copy; the handle's factor is untouched) and checks what the GPU sweeps
+ * rely on: supernodes that cover the rows in order with at most 32 rows each, ticket
+ * orders that are topological for the waits (edges of the elimination tree between
+ * supernodes), partial-sum slots in range and at most 8 entries per thread; then it replays
+ * the forward (L y = b) and the backward (L^T x = y) sweep over random asynchronous orders
+ * of ready supernodes, rows not yet final set to NaN, against plain substitution, for a
+ * right-hand side drawn from `seed`.  Runs on the host only (host_only handles too).
+ *   violations  out: broken invariants plus reads of rows not yet final (0 when sound)
+ *   rel_err     out: the larger relative L2 error of the two sweeps against substitution
+ * Errors: ARG (null pointers, beta_dt2 < 0, S not positive definite), STATE (a handle
+ * without a c-set: scheme IBFEM_CDM, or no cut cells). */
+int ibfem_check_solve_schedule(ibfem_t* h, double beta_dt2, uint64_t seed, int64_t* violations,
+                               double* rel_err);
+
 /* ---- allocation-free operator ----------------------------------------------------- */
 
 /* y = K x on the node lattice, for callers that cannot allocate device memory: an

@@ -13,6 +13,7 @@
 #include "host_setup.h"
 
 #include <algorithm>
+#include <limits>
 #include <array>
 #include <climits>
 #include <atomic>
@@ -918,7 +919,7 @@ namespace {
 // Supernode blocks of at most kMaxBlock rows: the GPU solves a block's dense diagonal part
 // from a warp's 32 x 32 shared-memory copy; longer runs become a chain of blocks of rising
 // height, whose couplings inside the run are off-block entries (solved row-parallel).
-constexpr int64_t kMaxBlock = 32;
+constexpr int64_t kMaxBlock = kImexSnMax;
 
 // Records a run of `size` consecutive rows as supernodes starting at height h0; returns the
 // height of its last block.
@@ -1393,6 +1394,133 @@ bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err)
         }
     if (!topo)
       for (size_t q = 0; q < nsn; ++q) sp.order[q] = (int32_t)(dir == 0 ? q : nsn - 1 - q);
+  }
+  return true;
+}
+
+bool imex_check_schedule(const Setup& s, const ImexData& part, double beta_dt2, uint64_t seed,
+                         int64_t& violations, double& rel_err, std::string& err) {
+  ImexData d = part;
+  if (!imex_factor(s, beta_dt2, d, err)) return false;
+  const SparseChol& L = d.chol;
+  const int64_t n = d.n_c;
+  const size_t nsn = d.sn_start.size();
+  violations = 0;
+  rel_err = 0.0;
+  if (n == 0) return true;
+  // the supernodes cover the rows once, in order, each within the GPU's block size
+  std::vector<int32_t> sn_of(n, -1);
+  int64_t next = 0;
+  for (size_t q = 0; q < nsn; ++q) {
+    if (d.sn_start[q] != next || d.sn_size[q] < 1 || d.sn_size[q] > kImexSnMax) ++violations;
+    for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q] && r < n; ++r) sn_of[r] = (int32_t)q;
+    next = d.sn_start[q] + d.sn_size[q];
+  }
+  if (next != n) ++violations;
+  if (violations) return true;
+  // a deterministic generator for the right-hand side and the schedules (splitmix64)
+  auto rnd = [&seed]() {
+    seed += 0x9e3779b97f4a7c15ULL;
+    uint64_t z = seed;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+  };
+  std::vector<double> b(n), y(n), x(n);
+  for (int64_t r = 0; r < n; ++r) b[r] = (double)(rnd() >> 11) * 0x1.0p-53 - 0.5;
+  // plain substitution: L y = b by rows (diagonal last), L^T x = y by rows of L^T (diagonal first)
+  for (int64_t r = 0; r < n; ++r) {
+    double a = b[r];
+    for (int64_t p = L.Lp[r]; p < L.Lp[r + 1] - 1; ++p) a -= L.Lx[p] * y[L.Li[p]];
+    y[r] = a / L.Lx[L.Lp[r + 1] - 1];
+  }
+  for (int64_t r = n - 1; r >= 0; --r) {
+    double a = y[r];
+    for (int64_t p = L.Up[r] + 1; p < L.Up[r + 1]; ++p) a -= L.Ux[p] * x[L.Ui[p]];
+    x[r] = a / L.Ux[L.Up[r]];
+  }
+  std::vector<double> cur, in = b;
+  for (int dir = 0; dir < 2; ++dir) {
+    const bool fwd = dir == 0;
+    const ImexSplit& sp = fwd ? d.fsplit : d.bsplit;
+    // the ticket order is topological for the waits
+    std::vector<int64_t> pos(nsn, -1);
+    for (size_t k = 0; k < sp.order.size(); ++k) pos[sp.order[k]] = (int64_t)k;
+    for (size_t q = 0; q < nsn; ++q) {
+      if (pos[q] < 0) ++violations;
+      for (int32_t k = sp.dep_ptr[q]; k < sp.dep_ptr[q + 1]; ++k)
+        if (pos[sp.dep[k]] >= pos[q]) ++violations;
+      // the work split: partial sums in range, at most kImexThreadEntries per thread
+      const int64_t g = sp.g[q];
+      if (g < 1 || g > kImexMaxSplit || (g > 1 && (sp.pbase[q] % 32 != 0 || sp.pbase[q] + 32 * g > sp.n_parts)))
+        ++violations;
+      for (int64_t r = d.sn_start[q]; r < d.sn_start[q] + d.sn_size[q]; ++r) {
+        const int64_t len = fwd ? d.f_off_end[r] - L.Lp[r] : L.Up[r + 1] - d.b_off_beg[r];
+        if (g < kImexMaxSplit && ((len + g - 1) / g + sp.tpr[q] - 1) / sp.tpr[q] > kImexThreadEntries) ++violations;
+      }
+    }
+    // random asynchronous schedules of ready supernodes; a row not yet final holds NaN, so a
+    // read that the waits do not cover poisons the result and is counted
+    cur.assign(n, std::numeric_limits<double>::quiet_NaN());
+    std::vector<char> done(nsn, 0);
+    size_t n_done = 0;
+    std::vector<int32_t> ready, run;
+    std::vector<std::pair<int64_t, double>> writes;
+    while (n_done < nsn) {
+      ready.clear();
+      for (size_t q = 0; q < nsn; ++q) {
+        if (done[q]) continue;
+        bool ok = true;
+        for (int32_t k = sp.dep_ptr[q]; k < sp.dep_ptr[q + 1] && ok; ++k) ok = done[sp.dep[k]] != 0;
+        if (ok) ready.push_back((int32_t)q);
+      }
+      if (ready.empty()) {   // a cycle of waits
+        ++violations;
+        return true;
+      }
+      run.clear();
+      for (int32_t q : ready)
+        if (rnd() % 3 == 0) run.push_back(q);
+      if (run.empty()) run.push_back(ready[rnd() % ready.size()]);
+      writes.clear();
+      for (int32_t q : run) {   // every supernode of a round reads before any of them writes
+        const int64_t st = d.sn_start[q];
+        const int wd = d.sn_size[q];
+        double T[kImexSnMax];
+        for (int i = 0; i < wd; ++i) {
+          const int64_t r = st + i;
+          const int64_t p0 = fwd ? L.Lp[r] : d.b_off_beg[r], p1 = fwd ? d.f_off_end[r] : L.Up[r + 1];
+          double acc = 0.0;
+          for (int64_t p = p0; p < p1; ++p) {
+            const int64_t c = fwd ? L.Li[p] : L.Ui[p];
+            if (c >= st && c < st + wd) ++violations;   // an in-block entry listed off-block
+            if (std::isnan(cur[c])) ++violations;
+            acc += (fwd ? L.Lx[p] : L.Ux[p]) * cur[c];
+          }
+          T[i] = in[r] - acc;
+        }
+        const double* M = (fwd ? d.sn_DT.data() : d.sn_D.data()) + d.sn_doff[q];
+        for (int jj = 0; jj < wd; ++jj) {
+          const int j = fwd ? jj : wd - 1 - jj;
+          const double xj = T[j] * M[(size_t)j * wd + j];
+          T[j] = xj;
+          for (int l = 0; l < wd; ++l)
+            if (fwd ? l > j : l < j) T[l] -= M[(size_t)j * wd + l] * xj;
+        }
+        for (int i = 0; i < wd; ++i) writes.push_back({st + i, T[i]});
+      }
+      for (const auto& w : writes) cur[w.first] = w.second;
+      for (int32_t q : run) done[q] = 1;
+      n_done += run.size();
+    }
+    const std::vector<double>& ref = fwd ? y : x;
+    double e2 = 0.0, r2 = 0.0;
+    for (int64_t r = 0; r < n; ++r) {
+      e2 += (cur[r] - ref[r]) * (cur[r] - ref[r]);
+      r2 += ref[r] * ref[r];
+    }
+    rel_err = std::max(rel_err, r2 > 0.0 ? std::sqrt(e2 / r2) : std::sqrt(e2));
+    in = cur;   // the backward sweep solves with the forward result
   }
   return true;
 }

@@ -121,6 +121,8 @@ bool sparse_cholesky(int64_t n, const std::vector<int64_t>& Ap, const std::vecto
 // sums are split over (beyond that the threads loop).
 constexpr int64_t kImexThreadEntries = 8;
 constexpr int64_t kImexMaxSplit = 256;
+// Rows of a supernode at most (the GPU solves its dense diagonal block in one warp).
+constexpr int kImexSnMax = 32;
 
 // One direction's sweep of the block solve (forward: L y = b; backward: L^T x = y): the
 // split of each supernode's off-block sums over CTAs, the supernodes each one waits for, and
@@ -173,6 +175,14 @@ struct ImexData {
 void imex_partition(const Setup& s, ImexData& d);
 // Factor S = M^cc + beta_dt2 K^cc; returns false (with message) if S is not positive definite.
 bool imex_factor(const Setup& s, double beta_dt2, ImexData& d, std::string& err);
+// Host check of the GPU block solve's schedule for S = M^cc + beta_dt2 K^cc (the partition
+// is copied and factored anew): supernode cover and size, topological ticket order, the
+// work split's bounds, and both sweeps replayed over random asynchronous orders of ready
+// supernodes (rows not yet final are NaN) against plain substitution.  Counts violations
+// and returns the larger relative error of the two sweeps; false if S is not positive
+// definite.
+bool imex_check_schedule(const Setup& s, const ImexData& part, double beta_dt2, uint64_t seed,
+                         int64_t& violations, double& rel_err, std::string& err);
 // Solve M^cc a = b (b and a in c-index order) with a Cholesky factor of M^cc.
 bool imex_mass_solve(const ImexData& d, const std::vector<double>& b, std::vector<double>& a,
                      std::string& err);

@@ -1311,6 +1311,19 @@ int ibfem_check_bounded_wait(ibfem_t* h, int polls) {
   IBFEM_CATCH
 }
 
+int ibfem_check_solve_schedule(ibfem_t* h, double beta_dt2, uint64_t seed, int64_t* violations,
+                               double* rel_err) {
+  if (!h) return fail(IBFEM_ERR_ARG, "null handle");
+  if (!violations || !rel_err || !(beta_dt2 >= 0.0)) return fail(IBFEM_ERR_ARG, "bad arguments");
+  if (!h->imex) return fail(IBFEM_ERR_STATE, "the handle solves no c-set (scheme IBFEM_CDM or no cut cells)");
+  IBFEM_TRY
+  std::string err;
+  if (!imex_check_schedule(h->setup, h->imex_host, beta_dt2, seed, *violations, *rel_err, err))
+    return fail(IBFEM_ERR_ARG, "S = M^cc + beta_dt2 K^cc is not positive definite: " + err);
+  return IBFEM_OK;
+  IBFEM_CATCH
+}
+
 int ibfem_set_state(ibfem_t* h, const double* u, const double* u_prev, int64_t step) {
   int rc = require_device(h);
   if (rc) return rc;

@@ -96,6 +96,8 @@ def lib():
         "ibfem_step": (C.c_int, [vp, C.c_int64]),
         "ibfem_sync": (C.c_int, [vp]),
         "ibfem_check_bounded_wait": (C.c_int, [vp, C.c_int]),
+        "ibfem_check_solve_schedule": (C.c_int, [vp, C.c_double, C.c_uint64, C.POINTER(C.c_int64),
+                                                 C.POINTER(C.c_double)]),
         "ibfem_step_timed": (C.c_int, [vp, C.c_int64, vp, C.c_size_t, DP, C.c_int, C.POINTER(C.c_int)]),
         "ibfem_kernel_name": (C.c_char_p, [vp, C.c_int]),
         "ibfem_sample": (C.c_int, [vp, C.c_int64, DP, C.POINTER(C.c_int64)]),
@@ -314,6 +316,14 @@ class Solver:
     def check_bounded_wait(self, polls):
         """Enqueue one bounded wait that runs out (``ibfem_check_bounded_wait``)."""
         _check(lib().ibfem_check_bounded_wait(self.h, int(polls)))
+
+    def check_solve_schedule(self, beta_dt2=0.0, seed=0):
+        """Host check of the GPU block solve's schedule (``ibfem_check_solve_schedule``):
+        returns (violations, larger relative error of the two sweeps against substitution)."""
+        v = C.c_int64()
+        e = C.c_double()
+        _check(lib().ibfem_check_solve_schedule(self.h, float(beta_dt2), int(seed), C.byref(v), C.byref(e)))
+        return int(v.value), float(e.value)
 
     def sample(self, max_rows):
         nr = self.n_obs * self.ncomp
