@@ -376,6 +376,19 @@ def algorithmic_bytes(inf, w):
 
 def roofline(prec, kname, kms, inf, w, peaks, r):
     n_dof, n_loc = inf.n_dof, inf.n_loc
+    if kname == "imex_solve":
+        # the c-set solve of Algorithm 2: both sweeps read L once (FP64 value + 32-bit column
+        # index per entry, the survey's 2 nnz(L) x 12 B), plus the residual gather and the
+        # correction's c-vectors; bound by its dependency chain, reported against HBM
+        nnz = int(inf.nnz_L)
+        byts = 2.0 * nnz * 12.0 + 6.0 * 8.0 * int(inf.n_c)
+        achieved = byts / (kms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": kname,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+                "algorithmic": f"2 nnz(L) x 12 B (nnz(L) = {nnz}) + 48 B per c-DOF ({int(inf.n_c)}) = {byts:.4e} B",
+                "note": "latency-bound: the sweeps follow the dissection tree's dependency chain"}
     if prec == "fp64":
         flops = 2.0 * n_loc * n_loc * inf.n_uncut + 6.0 * n_dof
         achieved = flops / (kms * 1e-3) / 1e12
@@ -489,13 +502,13 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel
     kname, kms = max(rb["kernels"].items(), key=lambda kv: kv[1])
     inf = rb["info"]
-    roof = roofline(best.split(":")[-1], kname, kms, inf, w, peaks, rb)
+    roof = roofline(parse_variant(best, w)[1], kname, kms, inf, w, peaks, rb)
     for p, r in results.items():
-        pv = p.split(":")[-1]
         if p == best:
             r["roofline"] = roof
-        elif pv in DTYPES:      # element-operator variants (not the IMEX / consistent-mass solves)
-            r["roofline"] = roofline(pv, *max(r["kernels"].items(), key=lambda kv: kv[1]), r["info"], w, peaks, r)
+        else:
+            r["roofline"] = roofline(parse_variant(p, w)[1], *max(r["kernels"].items(), key=lambda kv: kv[1]),
+                                     r["info"], w, peaks, r)
 
     # end to end through the C ABI with host buffers
     s = rb["solver"]

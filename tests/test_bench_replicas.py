@@ -112,3 +112,21 @@ def test_algorithmic_bytes_follow_the_roofline_model():
     b = bench.algorithmic_bytes(Inf(), Wl())
     assert b == 32 * 1873378 + 1281 * 50 * 51 * 4 + 4 * 65536
     assert abs(b - 73.3e6) < 0.05e6
+
+
+def test_imex_solve_roofline_counts_the_factor():
+    """The c-set solve is measured on the survey's model: both sweeps read L once (8 B value
+    and 4 B index per entry) plus 48 B per c-DOF of vectors."""
+    import bench
+
+    class Inf:
+        n_dof, n_loc, n_cut_matrices, nnz_L, n_c = 2092915, 16, 2564, 592535, 30765
+
+    class Wl:
+        dim, n, name = 2, (512, 512), "plate_holes_imex_512x512_p3"
+
+    r = bench.roofline("fp64", "imex_solve", 0.128, Inf(), Wl(), {"hbm_gbs": 6800.0}, {})
+    byts = 2 * 592535 * 12 + 48 * 30765
+    assert r["bound"] == "hbm" and r["kernel"] == "imex_solve"
+    assert abs(r["achieved"] - byts / 0.128e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-15
