@@ -328,7 +328,7 @@ def aggregate_replicas(step_ms, n_dof, world, device=None):
 # DRAM bytes of one CDM launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, cold
 # cache) of the current kernel code on the benchmark workload (profiles/ gives the command);
 # to be re-taken whenever the kernel changes
-MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.364288e6 + 2.308608e6,
+MEASURED_TRAFFIC = {("op_tc_exact_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 76.364288e6 + 2.137088e6,
                     ("op_tc_exact64_fused_cdm", "plate_holes_elastic_256x256_p4", 0): 51.207424e6 + 0.105984e6}
 
 # arithmetic of each variant's element operator (the state and the update are FP64 in all)
