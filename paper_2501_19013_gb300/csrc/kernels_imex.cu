@@ -239,7 +239,6 @@ __global__ void __launch_bounds__(kLevelThreads) imex_sweep_kernel(DevProblem pb
   if (lane == 0) st_release_u32(sp.done + tk.sn, ep);
 }
 
-
 // gather b[r] = in[c_dof[perm[r]]] * scal into work, or scatter out[c_dof[perm[r]]] = work[r]
 __global__ void __launch_bounds__(256) imex_gather_kernel(ImexDev im, const double* __restrict__ in,
                                                           const double* __restrict__ scal) {
