@@ -139,8 +139,8 @@ typedef struct {
     int64_t n_elem, n_uncut, n_cut, n_outside;
     int64_t n_c;              /* IMEX: DOFs treated implicitly (0 for CDM)             */
     int64_t nnz_L;            /* IMEX: nonzeros of the Cholesky factor                 */
-    int32_t n_levels;         /* IMEX: sequential block steps of one triangular solve
-                                 (heights of the nested-dissection tree: one launch each)*/
+    int32_t n_levels;         /* IMEX: heights of the nested-dissection tree, the
+                                 longest chain of waits in one triangular sweep       */
     int32_t n_loc;            /* DOFs per element                                      */
     int32_t ncomp;
     int32_t precision;
